@@ -1,0 +1,55 @@
+"""Shared test plumbing: build oracle lattices from the seeded workloads, and measure errors."""
+import numpy as np
+
+from oracle import OracleLattice, TimeFn
+
+
+def oracle_time_fn(fn):
+    return TimeFn(fn.kind, fn.amplitude, fn.period, fn.phase, fn.table)
+
+
+def oracle_from_workload(w, threads=1, eps0=0.0, mu0=0.0, init=True):
+    L = OracleLattice(w.model, w.shape, w.eps_r, w.mu_r, w.sigma, eps0=eps0, mu0=mu0, threads=threads)
+    for s in w.sources:
+        if s.kind == "current":
+            L.add_current(s.cells, s.w, oracle_time_fn(s.fn))
+        else:
+            L.add_impose(s.cells, s.E0, s.B0, oracle_time_fn(s.fn))
+    if init:
+        E = np.zeros((3, w.n)) if w.E is None else w.E
+        B = np.zeros((3, w.n)) if w.B is None else w.B
+        L.init_fields(E, B)
+    return L
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a - b))
+
+
+def operator_matrix(L):
+    """The oracle's one-step map as a dense matrix, column c = step(unit vector c)."""
+    n = L.n * L.q
+    G = np.zeros((n, n))
+    for c in range(n):
+        u = np.zeros(n)
+        u[c] = 1.0
+        L.set_populations(u.reshape(L.q, L.n), 0)
+        L.step(1)
+        G[:, c] = L.populations().reshape(-1)
+    return G
+
+
+def peak_interp(y):
+    """Signed value at the largest |y| sample, refined by a parabola through its two neighbours."""
+    i = int(np.argmax(np.abs(y)))
+    if i == 0 or i == len(y) - 1:
+        return float(y[i])
+    ym, y0, yp = y[i - 1], y[i], y[i + 1]
+    den = ym - 2 * y0 + yp
+    if den == 0:
+        return float(y0)
+    off = 0.5 * (ym - yp) / den
+    return float(y0 - 0.25 * (ym - yp) * off)
