@@ -1,0 +1,363 @@
+"""Benchmark: lattice updates per second of the MM and HV time steps on the Hertz-dipole workload.
+
+Workload (one GPU): a 256^3 vacuum lattice per model with the Section IV-C Gaussian dipole current
+(J0 = 1e-4, alpha = 0.5, period 32 steps), FP32 populations. One benchmark step = one MM time step
+on its lattice plus one HV time step on its lattice (the whole fused update of every cell, source
+cells included). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
+
+Under torchrun (N > 1) every rank runs its own pair of lattices (independent problems, weak
+scaling, no data-path collective); timing is the maximum over ranks. ``--impl reference`` times
+the FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2309_08068_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "MLUPS"
+BYTES_PER_CELL = {"mm": 384, "hv": 288}  # FP32 populations read + written; vacuum needs no media bytes
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2309_08068_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(kernel: str, n_cells: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to n_cells, or None
+    when the summary is missing or was taken on a different kernel source."""
+    try:
+        with open(PROFILE_FILE) as fh:
+            prof = json.load(fh)
+    except Exception:
+        return None
+    entry = prof.get(kernel)
+    if not entry or entry.get("source_hash") != kernel_source_hash():
+        return None
+    return entry["dram_bytes_per_launch"] * n_cells / entry["cells"]
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells_per_rank_step: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job MLUPS: every rank updates its own lattices (weak scaling), divided by the slowest
+    rank's time."""
+    return cells_per_rank_step * steps * world / seconds / 1e6
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores, bounded sample
+# ------------------------------------------------------------------------------------------------
+
+def oracle_mlups(n_side: int, budget_s: float, threads: int, steps: int | None = None, warmup: int = 1):
+    """Time the oracle on an n_side^3 dipole lattice per model; returns (MLUPS, steps, seconds)."""
+    from oracle import OracleLattice, TimeFn
+    total_updates = 0
+    total_s = 0.0
+    done = {}
+    for model in ("mm", "hv"):
+        w = wl.hertz_dipole(model, n=n_side)
+        L = OracleLattice(model, w.shape, threads=threads)
+        s = w.sources[0]
+        L.add_current(s.cells, s.w, TimeFn("sin", s.fn.amplitude, s.fn.period, s.fn.phase))
+        L.init_fields(np.zeros((3, w.n)), np.zeros((3, w.n)))
+        L.step(warmup)
+        k = 0
+        t0 = time.perf_counter()
+        while True:
+            L.step(1)
+            k += 1
+            el = time.perf_counter() - t0
+            if (steps is not None and k >= steps) or (steps is None and el >= budget_s / 2):
+                break
+        total_updates += w.n * k
+        total_s += el
+        done[model] = k
+    return total_updates / total_s / 1e6, done, total_s
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = cpu_cores()
+    side = 48
+    mlups, per_model, secs = oracle_mlups(side, 0.0, cores, steps=args.warmup + args.steps, warmup=0)
+    # each benchmark step is one MM and one HV step on a 48^3 sample of the dipole workload
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "Mcell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / (args.warmup + args.steps), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"hertz_dipole_{args.n}^3_mm+hv", "sample": f"{side}^3 lattice per model",
+                   "parallelism": "cpu threads"},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{side}^3 dipole lattice per model, {args.warmup + args.steps} steps each"},
+        "e2e": {"value": round(mlups, 4), "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+
+    n_side = args.n
+    ncell = n_side ** 3
+    stream = torch.cuda.Stream()
+    lats = {}
+    with torch.cuda.stream(stream):
+        for model in ("mm", "hv"):
+            w = wl.hertz_dipole(model, n=n_side, period=32.0)
+            lats[model] = lattice_from_workload(w, stream=stream)
+    torch.cuda.synchronize()
+
+    def one_step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        lats["mm"].step(1)
+        if ev is not None:
+            ev[1].record(stream)
+        lats["hv"].step(1)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches0 = sum(L.launch_count for L in lats.values())
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for k in range(args.steps):
+            one_step(events[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = sum(L.launch_count for L in lats.values()) - launches0
+    elapsed_ms = start.elapsed_time(stop)
+    mm_ms = sum(e[0].elapsed_time(e[1]) for e in events) / args.steps
+    hv_ms = sum(e[1].elapsed_time(e[2]) for e in events) / args.steps
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    finite = all(L.check_finite() for L in lats.values())
+
+    # end to end through the C ABI with host buffers: upload fields, K steps, read E and B back
+    pinned_E = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
+    pinned_B = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
+    out = {m: np.empty((2, 3, ncell), np.float32) for m in lats}
+    e2e_steps = args.steps
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m, L in lats.items():
+        L.lib.lbm_init_fields(L.h, pinned_E.data_ptr(), pinned_B.data_ptr(), 0)
+    for _ in range(e2e_steps):
+        lats["mm"].step(1)
+        lats["hv"].step(1)
+    for m, L in lats.items():
+        L._check(L.lib.lbm_fields(L.h, 3, out[m].ctypes.data, 0))
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    h2d = 2 * 2 * 3 * ncell * 4
+    d2h = 2 * 2 * 3 * ncell * 4
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    value = job_value(2 * ncell, args.steps, world, elapsed_ms * 1e-3)
+    peak, peak_kind = hbm_peak()
+    mm_gbs = BYTES_PER_CELL["mm"] * ncell / (mm_ms * 1e-3) / 1e9
+    hv_gbs = BYTES_PER_CELL["hv"] * ncell / (hv_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("mm_step_kernel", ncell)
+    cores = cpu_cores()
+    cpu_mlups, cpu_steps, cpu_s = oracle_mlups(64, args.cpu_seconds, cores)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"hertz_dipole_{n_side}^3_mm+hv", "cells_per_model": ncell,
+                   "step": "one MM step + one HV step, each on its own lattice", "period": 32, "J0": 1e-4,
+                   "l2": "inputs larger than L2 (MM 3.2 GB, HV 2.4 GB per population buffer)",
+                   "parallelism": f"independent lattices per rank x{world}"},
+        "per_model": {
+            "mm": {"MLUPS": round(ncell / (mm_ms * 1e-3) / 1e6, 2), "ms_per_step": round(mm_ms, 4),
+                   "algorithmic_GBps": round(mm_gbs, 1), "bytes_per_cell": BYTES_PER_CELL["mm"]},
+            "hv": {"MLUPS": round(ncell / (hv_ms * 1e-3) / 1e6, 2), "ms_per_step": round(hv_ms, 4),
+                   "algorithmic_GBps": round(hv_gbs, 1), "bytes_per_cell": BYTES_PER_CELL["hv"],
+                   "frac": round(hv_gbs / peak, 4)},
+        },
+        "roofline": {"bound": "hbm", "kernel": "mm_step_kernel (+ source-cell launch)",
+                     "achieved": round(mm_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(mm_gbs / peak, 4),
+                     "traffic": None if traffic is None else round(traffic)},
+        "cpu_baseline": {"value": round(cpu_mlups, 4), "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"64^3 dipole lattice per model, FP64, {cpu_steps} steps, {cpu_s:.1f} s"},
+        "e2e": {"value": round(job_value(2 * ncell, e2e_steps, world, e2e_s), 2), "unit": "Mcell-updates/s",
+                "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+                "job": f"lbm_init_fields from pinned host E, B + {e2e_steps} steps + lbm_fields E, B to host"},
+        "gpu_launches": int(launches),
+        "finite": finite,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2309_08068_gb300 import build
+        build.build()
+        import oracle
+        oracle.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

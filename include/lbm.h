@@ -1,0 +1,181 @@
+/*
+ * lbm.h - C ABI of liblbm.so: GB300 (sm_103a) time stepping of the two lattice-Boltzmann Maxwell
+ * schemes compared in arXiv 2309.08068, the Mendoza-Munoz model (MM, Section II) and the modified
+ * Hauser-Verhey model (HV, Section III with the source term of eq. SourceTermHV).
+ *
+ * One context holds one periodic nx x ny x nz lattice on the current CUDA device. Cells are indexed
+ * x + nx * (y + ny * z) (x fastest). Vector fields are component-major: component c of cell i is at
+ * [c * n + i]. All device work runs on the context's CUDA stream, in order.
+ *
+ * Error behaviour: every call returns LBM_OK (0) or a negative LBM_E* code; nothing aborts or
+ * traps. lbm_last_error() gives a message for the last failing call on a context. A context is not
+ * thread-safe: one host thread at a time.
+ *
+ * Ownership: the library copies every input array at the call (media, sources, initial fields) and
+ * never keeps a caller pointer. Outputs go to caller buffers. Device buffers passed with
+ * on_device = 1 must be device (or managed) memory of the context's device.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Models. LBM_MM: D3Q13 velocities with electric and magnetic distributions, 48 moving + 2 rest
+ * populations per cell (Section II). LBM_HV: D3Q7 velocities with a vector electric e_i and a vector
+ * magnetic h_i distribution per direction, 36 scalars per cell (Section III). */
+enum { LBM_MM = 0, LBM_HV = 1 };
+
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,       /* bad argument (null pointer, size, index, unknown enum) */
+    LBM_ENOMEM = -2,       /* device or host allocation failed */
+    LBM_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    LBM_ENONFINITE = -4,   /* lbm_check_finite found a NaN or infinity */
+    LBM_ETIMEDOUT = -5,    /* reserved for bounded waits */
+    LBM_EUNSUPPORTED = -6  /* valid request this build does not implement */
+};
+
+/* Population storage precision. Only LBM_F32 is implemented; arithmetic is always FP32. */
+enum { LBM_F32 = 0, LBM_BF16 = 1, LBM_F16 = 2 };
+
+/* Per-cell linear media (Section I-B remark: eps = eps_r eps0, mu = mu_r mu0). Each pointer is an
+ * array of n floats, or NULL for the uniform default eps_r = 1, mu_r = 1, sigma = 0. on_device
+ * selects device or host memory for all three. Requirements: eps_r > 0, mu_r > 0, sigma >= 0,
+ * finite. When the lattice holds at most 256 distinct (eps_r, mu_r, sigma) triples the library
+ * stores one byte per cell and a material table; otherwise it stores the three per-cell arrays. */
+typedef struct {
+    const float* eps_r;
+    const float* mu_r;
+    const float* sigma;
+    int on_device;
+} lbm_media;
+
+/* Context options; pass NULL for all defaults.
+ * storage: LBM_F32.  cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * track_rho: MM only; also store the rest populations f_0^(0), f_0^(1), so that rho_c (eq.
+ *   MacroscopicFieldsMiller) is kept and lbm_get_populations returns them. Otherwise the rest
+ *   populations are not stored (neither enters E, B, D, H or J) and read back as 0.
+ * eps0, mu0: vacuum constants; 0 selects the model default. MM fixes eps0 = 1, mu0 = 2 (Section
+ *   II-A; any other value gives LBM_EUNSUPPORTED). HV default eps0 = mu0 = 3: the paper fixes only
+ *   the vacuum speed 1/sqrt(eps0 mu0) = 1/3 (Section III-A), which the split does not change. */
+typedef struct {
+    int storage;
+    void* cuda_stream;
+    int track_rho;
+    double eps0;
+    double mu0;
+} lbm_options;
+
+/* Time dependence s(t) of a source, evaluated on the host in double precision for iteration t.
+ *   LBM_FN_SIN:   amplitude * sin(2 pi t / period + phase)
+ *   LBM_FN_TABLE: amplitude * table[t] for 0 <= t < table_len, else 0 (table copied at the call)
+ *   LBM_FN_CONST: amplitude */
+enum { LBM_FN_SIN = 0, LBM_FN_TABLE = 1, LBM_FN_CONST = 2 };
+typedef struct {
+    int kind;
+    double amplitude;
+    double period;
+    double phase;
+    const double* table;
+    int64_t table_len;
+} lbm_time_fn;
+
+/* Sources (Section IV-B/C and the Appendix B note).
+ *   LBM_SRC_CURRENT: external current J_ext(x, t) = w(x) s(t) at the listed cells; w holds 3 floats
+ *     per cell. MM feeds it to eq. MacroscopicEMiller and the equilibria; HV to J = sigma E + J_ext
+ *     and the source term T_i = -(J . v_i) v_i / 2.
+ *   LBM_SRC_IMPOSE: after each collision the listed cells are set to the equilibrium of
+ *     E = E0 s(t), B = B0 s(t), J = 0 (Appendix B "impose fields"); MM's rest populations keep their
+ *     collided values.
+ * Several sources may share cells: currents add, imposed fields add. cells[] are in [0, n); host
+ * memory; copied at the call. At most LBM_MAX_SOURCES sources per context. */
+enum { LBM_SRC_CURRENT = 0, LBM_SRC_IMPOSE = 1 };
+#define LBM_MAX_SOURCES 16
+typedef struct {
+    int kind;
+    int64_t n_cells;
+    const int64_t* cells;
+    const float* w;
+    float E0[3];
+    float B0[3];
+    lbm_time_fn fn;
+} lbm_source;
+
+/* Field selection for lbm_fields; output blocks follow in this order, each 3 x n floats. */
+enum { LBM_FIELD_E = 1, LBM_FIELD_B = 2, LBM_FIELD_D = 4, LBM_FIELD_H = 8, LBM_FIELD_J = 16 };
+
+/* Create a context for `model` on an nx x ny x nz periodic lattice (every axis >= 1; dimensions of 1
+ * are allowed and make that axis trivially periodic). Allocates two population buffers (pull
+ * scheme, A/B) on the current device and leaves them zero; t = 0. */
+int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const lbm_options* opts,
+               lbm_ctx** out);
+
+/* Appendix B, first lines: every population := its equilibrium for the given E and B with J = 0
+ * (MM: D' = eps_r E, eq. MacroscopicEMiller with J = 0; HV: D = eps0 eps_r E); rest populations 0;
+ * t := 0. E and B are 3 x n floats, host (on_device = 0) or device memory. Synchronous for host
+ * input; stream-ordered for device input. */
+int lbm_init_fields(lbm_ctx* ctx, const float* E, const float* B, int on_device);
+
+/* Add one source (see lbm_source). Takes effect from the next lbm_step. */
+int lbm_set_source(lbm_ctx* ctx, const lbm_source* src);
+/* Remove every source. */
+int lbm_clear_sources(lbm_ctx* ctx);
+
+/* Enqueue n >= 0 time steps on the context stream and return without waiting. Iteration t (t = 1,
+ * 2, ... counted from lbm_init_fields) evaluates the sources at s(t). Each step is the fused MM or HV
+ * update of every cell: pull the neighbours' post-collision populations, form the moments (eqs.
+ * MacroscopicFieldsMiller / MacroscopicFieldsHV), compute E and J (eqs. MacroscopicEMiller,
+ * MacorscopicCurrentMiller / E = D/eps, J = sigma E + J_ext), the equilibria (eqs.
+ * equilibriumsMiller / equilibriumHV), the tau = 1/2 collision (eqs. CollisionMiller /
+ * CollisionmodifiedHV), the imposed cells, and store. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Fields at the current time t: moments of the current populations, with the external current of
+ * iteration t + 1 (the one the next collision uses). For each bit of mask in the order E, B, D, H, J,
+ * 3 x n floats are written to out. MM: D = eps0 eps_r E, H = B / (mu0 mu_r). HV: D and B are the
+ * moments, E = D / eps, H = B / mu. Host output (on_device = 0) waits for the stream; device output
+ * is stream-ordered. */
+int lbm_fields(lbm_ctx* ctx, unsigned mask, float* out, int on_device);
+
+/* Number of populations per cell in the canonical layout: MM 50, HV 36. */
+int lbm_num_populations(int model);
+
+/* Populations f(x, t) before the next collision, canonical layout out[k * n + cell]:
+ *   MM: k = r*24 + p*8 + (i-1)*2 + j for the moving ones (r = 0 electric, 1 magnetic; plane p = 0..2;
+ *       i = 1..4; j = 0..1, eq. VelocitySetMiller / ElectromagneticVectorsMiller), k = 48: f_0^(0),
+ *       k = 49: f_0^(1) (0 unless track_rho).
+ *   HV: k = r*18 + (i-1)*3 + c (r = 0: e_i, 1: h_i; i = 1..6 in the Section III order; c = x, y, z).
+ * Host output waits for the stream. */
+int lbm_get_populations(lbm_ctx* ctx, float* out, int on_device);
+/* Load populations in the same layout and set the time to t (checkpoint restore). */
+int lbm_set_populations(lbm_ctx* ctx, const float* in, int on_device, int64_t t);
+
+/* Double-precision reductions over the lattice (waits for the stream):
+ *   out[0] = field energy (1/2) sum_x (E . D + B . H),  out[1] = sum of squared populations,
+ *   out[2] = MM total charge sum_x rho_c (0 unless track_rho; 0 for HV). */
+int lbm_reduce(lbm_ctx* ctx, double out[3]);
+/* LBM_OK if every stored population is finite, LBM_ENONFINITE otherwise. Waits for the stream. */
+int lbm_check_finite(lbm_ctx* ctx);
+
+/* Number of completed steps. */
+int64_t lbm_time(const lbm_ctx* ctx);
+/* Kernel launches enqueued by this context so far (all kinds). */
+int64_t lbm_launch_count(const lbm_ctx* ctx);
+/* Message of the last failing call on ctx (or of the last failing lbm_create when ctx is NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+/* Wait for the context stream. */
+int lbm_sync(lbm_ctx* ctx);
+/* Free the context and its device memory. NULL is accepted. */
+int lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

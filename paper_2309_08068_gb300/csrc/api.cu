@@ -1,0 +1,705 @@
+// C-ABI of liblbm.so (declared in include/lbm.h): context lifecycle, argument checks, media
+// compression, source bookkeeping and kernel dispatch. No call aborts; every failure returns an
+// LBM_E* code with a message kept on the context.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+namespace {
+
+struct HostSource {
+    int kind;
+    std::vector<int> cells;
+    std::vector<float> w;  // 3 per cell (current)
+    float E0[3], B0[3];
+    lbm_time_fn fn;
+    std::vector<double> table;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct lbm_ctx {
+    int model = 0;
+    Geometry g{};
+    cudaStream_t stream = nullptr;
+    int track_rho = 0;
+    double eps0 = 0, mu0 = 0;
+    int device = 0;
+    // populations (pull scheme, two buffers)
+    void* buf[2] = {nullptr, nullptr};   // MM float4[12][n]; HV float4[6][n]
+    void* buf2[2] = {nullptr, nullptr};  // HV float2[6][n]
+    float* rho[2] = {nullptr, nullptr};  // MM f_0^(0) (track_rho)
+    float* rest1 = nullptr;              // MM f_0^(1) (track_rho)
+    int cur = 0;
+    // media
+    int media_mode = kUniform;
+    float4 uniform = make_float4(1.f, 1.f, 0.f, 0.f);
+    uint8_t* mat_id = nullptr;
+    float4* mat_table = nullptr;
+    float* eps_r = nullptr;
+    float* mu_r = nullptr;
+    float* sigma = nullptr;
+    // sources
+    std::vector<HostSource> sources;
+    int n_special = 0;
+    int* d_cell = nullptr;
+    int* d_entry_begin = nullptr;
+    int* d_entry_src = nullptr;
+    float* d_entry_w = nullptr;
+    uint32_t* d_impose_mask = nullptr;
+    // reductions
+    double* d_partials = nullptr;
+    double* d_result = nullptr;
+    int reduce_blocks = 0;
+    int partial_capacity = 0;  // blocks
+    int64_t t = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_ctx* ctx, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                         \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail((ctx), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int check_launch(lbm_ctx* ctx, int launched) {
+    ctx->launches += launched;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+
+int ensure_device(lbm_ctx* ctx) {
+    int dev = -1;
+    CUDA_TRY(ctx, cudaGetDevice(&dev));
+    if (dev != ctx->device) CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return LBM_OK;
+}
+
+size_t group_bytes(int model) { return model == LBM_MM ? 12 * sizeof(float4) : 6 * sizeof(float4); }
+
+StepArgs base_args(lbm_ctx* c) {
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = c->g;
+    a.media_mode = c->media_mode;
+    a.media.uniform = c->uniform;
+    a.media.id = c->mat_id;
+    a.media.table = c->mat_table;
+    a.media.eps_r = c->eps_r;
+    a.media.mu_r = c->mu_r;
+    a.media.sigma = c->sigma;
+    a.sv.n_special = c->n_special;
+    a.sv.cell = c->d_cell;
+    a.sv.entry_begin = c->d_entry_begin;
+    a.sv.entry_src = c->d_entry_src;
+    a.sv.entry_w = c->d_entry_w;
+    a.sv.impose_mask = c->d_impose_mask;
+    for (size_t k = 0; k < c->sources.size(); ++k) {
+        for (int q = 0; q < 3; ++q) {
+            a.sc.E0[k][q] = c->sources[k].E0[q];
+            a.sc.B0[k][q] = c->sources[k].B0[q];
+        }
+    }
+    a.eps0 = (float)c->eps0;
+    a.mu0 = (float)c->mu0;
+    return a;
+}
+
+// Current buffer as input (fin*) and the other as output (fout*).
+void bind_buffers(lbm_ctx* c, StepArgs& a, int in, int out) {
+    a.fin = c->buf[in];
+    a.fout = c->buf[out];
+    if (c->model == LBM_HV) {
+        a.fin2 = c->buf2[in];
+        a.fout2 = c->buf2[out];
+    } else {
+        a.fin2 = c->rest1;
+        a.fout2 = c->rest1;
+    }
+    a.rho_in = c->rho[in];
+    a.rho_out = c->rho[out];
+}
+
+double time_value(const HostSource& s, int64_t t) {
+    const double pi = 3.14159265358979323846;
+    switch (s.fn.kind) {
+        case LBM_FN_SIN: return s.fn.amplitude * std::sin(2.0 * pi * (double)t / s.fn.period + s.fn.phase);
+        case LBM_FN_TABLE:
+            return (t >= 0 && t < (int64_t)s.table.size()) ? s.fn.amplitude * s.table[(size_t)t] : 0.0;
+        default: return s.fn.amplitude;
+    }
+}
+
+void fill_scalars(lbm_ctx* c, StepArgs& a, int64_t t) {
+    for (size_t k = 0; k < c->sources.size(); ++k) a.sc.s[k] = (float)time_value(c->sources[k], t);
+}
+
+template <class T>
+void free_dev(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void free_sources_device(lbm_ctx* c) {
+    free_dev(c->d_cell);
+    free_dev(c->d_entry_begin);
+    free_dev(c->d_entry_src);
+    free_dev(c->d_entry_w);
+    free_dev(c->d_impose_mask);
+    c->n_special = 0;
+}
+
+int ensure_partials(lbm_ctx* c, int blocks) {
+    if (blocks <= c->partial_capacity) return LBM_OK;
+    free_dev(c->d_partials);
+    c->partial_capacity = 0;
+    if (cudaMalloc(&c->d_partials, sizeof(double) * 3 * (size_t)blocks) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LBM_ENOMEM, "cannot allocate %d reduction partials", blocks);
+    }
+    c->partial_capacity = blocks;
+    return LBM_OK;
+}
+
+// Merge every source into one sorted list of special cells with CSR current entries and an
+// imposing-source bitmask, and upload it.
+int rebuild_sources(lbm_ctx* c) {
+    free_sources_device(c);
+    std::map<int, std::pair<std::vector<std::pair<int, int>>, uint32_t>> cells;  // cell -> (entries, mask)
+    for (size_t k = 0; k < c->sources.size(); ++k) {
+        const HostSource& s = c->sources[k];
+        for (size_t m = 0; m < s.cells.size(); ++m) {
+            auto& slot = cells[s.cells[m]];
+            if (s.kind == LBM_SRC_CURRENT) slot.first.emplace_back((int)k, (int)m);
+            else slot.second |= (1u << k);
+        }
+    }
+    if (cells.empty()) return LBM_OK;
+    std::vector<int> cell, begin, src;
+    std::vector<float> w;
+    std::vector<uint32_t> mask;
+    begin.push_back(0);
+    for (auto& kv : cells) {
+        cell.push_back(kv.first);
+        for (auto& e : kv.second.first) {
+            src.push_back(e.first);
+            const HostSource& s = c->sources[(size_t)e.first];
+            for (int q = 0; q < 3; ++q) w.push_back(s.w[3 * (size_t)e.second + q]);
+        }
+        begin.push_back((int)src.size());
+        mask.push_back(kv.second.second);
+    }
+    const int ns = (int)cell.size();
+    const size_t ne = std::max<size_t>(src.size(), 1);
+    if (cudaMalloc(&c->d_cell, sizeof(int) * ns) != cudaSuccess ||
+        cudaMalloc(&c->d_entry_begin, sizeof(int) * (ns + 1)) != cudaSuccess ||
+        cudaMalloc(&c->d_entry_src, sizeof(int) * ne) != cudaSuccess ||
+        cudaMalloc(&c->d_entry_w, sizeof(float) * 3 * ne) != cudaSuccess ||
+        cudaMalloc(&c->d_impose_mask, sizeof(uint32_t) * ns) != cudaSuccess) {
+        cudaGetLastError();
+        free_sources_device(c);
+        return fail(c, LBM_ENOMEM, "cannot allocate the source-cell list (%d cells)", ns);
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_cell, cell.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_entry_begin, begin.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+    if (!src.empty()) {
+        CUDA_TRY(c, cudaMemcpy(c->d_entry_src, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_entry_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_impose_mask, mask.data(), sizeof(uint32_t) * ns, cudaMemcpyHostToDevice));
+    c->n_special = ns;
+    return LBM_OK;
+}
+
+// Copy a (possibly device) float array of n values to the host.
+int fetch_host(lbm_ctx* c, const float* p, int on_device, int64_t n, std::vector<float>& out) {
+    out.resize((size_t)n);
+    if (on_device) CUDA_TRY(c, cudaMemcpy(out.data(), p, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost));
+    else memcpy(out.data(), p, sizeof(float) * (size_t)n);
+    return LBM_OK;
+}
+
+int setup_media(lbm_ctx* c, const lbm_media* m) {
+    const int64_t n = c->g.n;
+    if (!m || (!m->eps_r && !m->mu_r && !m->sigma)) {
+        c->media_mode = kUniform;
+        c->uniform = make_float4(1.f, 1.f, 0.f, 0.f);
+        return LBM_OK;
+    }
+    std::vector<float> er, mr, sg;
+    int rc;
+    if (m->eps_r && (rc = fetch_host(c, m->eps_r, m->on_device, n, er)) != LBM_OK) return rc;
+    if (m->mu_r && (rc = fetch_host(c, m->mu_r, m->on_device, n, mr)) != LBM_OK) return rc;
+    if (m->sigma && (rc = fetch_host(c, m->sigma, m->on_device, n, sg)) != LBM_OK) return rc;
+    auto val = [&](const std::vector<float>& v, int64_t i, float dflt) { return v.empty() ? dflt : v[(size_t)i]; };
+    std::map<std::tuple<float, float, float>, int> ids;
+    std::vector<uint8_t> id((size_t)n);
+    bool table_ok = true;
+    for (int64_t i = 0; i < n; ++i) {
+        const float e = val(er, i, 1.f), u = val(mr, i, 1.f), s = val(sg, i, 0.f);
+        if (!(std::isfinite(e) && e > 0.f) || !(std::isfinite(u) && u > 0.f) || !(std::isfinite(s) && s >= 0.f))
+            return fail(c, LBM_EINVAL, "cell %lld: need finite eps_r > 0, mu_r > 0, sigma >= 0 (got %g, %g, %g)",
+                        (long long)i, e, u, s);
+        if (!table_ok) continue;
+        auto key = std::make_tuple(e, u, s);
+        auto it = ids.find(key);
+        if (it == ids.end()) {
+            if (ids.size() == 256) {
+                table_ok = false;
+                continue;
+            }
+            it = ids.emplace(key, (int)ids.size()).first;
+        }
+        id[(size_t)i] = (uint8_t)it->second;
+    }
+    if (table_ok && ids.size() == 1) {
+        auto key = ids.begin()->first;
+        c->media_mode = kUniform;
+        c->uniform = make_float4(std::get<0>(key), std::get<1>(key), std::get<2>(key), 0.f);
+        return LBM_OK;
+    }
+    if (table_ok) {
+        std::vector<float4> table(ids.size());
+        for (auto& kv : ids)
+            table[(size_t)kv.second] =
+                make_float4(std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), 0.f);
+        if (cudaMalloc(&c->mat_id, (size_t)n) != cudaSuccess ||
+            cudaMalloc(&c->mat_table, sizeof(float4) * table.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LBM_ENOMEM, "cannot allocate the material table");
+        }
+        CUDA_TRY(c, cudaMemcpy(c->mat_id, id.data(), (size_t)n, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->mat_table, table.data(), sizeof(float4) * table.size(), cudaMemcpyHostToDevice));
+        c->media_mode = kTable;
+        return LBM_OK;
+    }
+    c->media_mode = kPerCell;
+    float** dst[3] = {&c->eps_r, &c->mu_r, &c->sigma};
+    const std::vector<float>* srcv[3] = {&er, &mr, &sg};
+    const float dflt[3] = {1.f, 1.f, 0.f};
+    for (int q = 0; q < 3; ++q) {
+        if (cudaMalloc(dst[q], sizeof(float) * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LBM_ENOMEM, "cannot allocate per-cell media");
+        }
+        std::vector<float> v = srcv[q]->empty() ? std::vector<float>((size_t)n, dflt[q]) : *srcv[q];
+        CUDA_TRY(c, cudaMemcpy(*dst[q], v.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice));
+    }
+    return LBM_OK;
+}
+
+void release(lbm_ctx* c) {
+    for (int b = 0; b < 2; ++b) {
+        free_dev(c->buf[b]);
+        free_dev(c->buf2[b]);
+        free_dev(c->rho[b]);
+    }
+    free_dev(c->rest1);
+    free_dev(c->mat_id);
+    free_dev(c->mat_table);
+    free_dev(c->eps_r);
+    free_dev(c->mu_r);
+    free_dev(c->sigma);
+    free_sources_device(c);
+    free_dev(c->d_partials);
+    free_dev(c->d_result);
+}
+
+// Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
+int stage_input(lbm_ctx* c, const float* p, int on_device, size_t count, float** dev, bool* owned) {
+    if (on_device) {
+        *dev = const_cast<float*>(p);
+        *owned = false;
+        return LBM_OK;
+    }
+    if (cudaMalloc(dev, sizeof(float) * count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LBM_ENOMEM, "cannot allocate a staging buffer of %zu floats", count);
+    }
+    *owned = true;
+    CUDA_TRY(c, cudaMemcpyAsync(*dev, p, sizeof(float) * count, cudaMemcpyHostToDevice, c->stream));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_num_populations(int model) { return model == LBM_MM ? 50 : (model == LBM_HV ? 36 : LBM_EINVAL); }
+
+int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const lbm_options* opts, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "lbm_create: out is NULL");
+    *out = nullptr;
+    if (model != LBM_MM && model != LBM_HV) return fail(nullptr, LBM_EINVAL, "lbm_create: unknown model %d", model);
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: dimensions must be >= 1");
+    const int64_t n = (int64_t)nx * ny * nz;
+    if (n > (int64_t)INT32_MAX) return fail(nullptr, LBM_EINVAL, "lbm_create: %lld cells exceed 2^31 - 1", (long long)n);
+    if (opts && opts->storage != LBM_F32)
+        return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only LBM_F32 population storage is built");
+    double eps0 = opts ? opts->eps0 : 0.0, mu0 = opts ? opts->mu0 : 0.0;
+    if (eps0 < 0 || mu0 < 0 || !std::isfinite(eps0) || !std::isfinite(mu0))
+        return fail(nullptr, LBM_EINVAL, "lbm_create: eps0, mu0 must be >= 0");
+    if (model == LBM_MM) {
+        if ((eps0 != 0 && eps0 != 1.0) || (mu0 != 0 && mu0 != 2.0))
+            return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: the MM model fixes eps0 = 1, mu0 = 2");
+        eps0 = 1.0;
+        mu0 = 2.0;
+    } else {
+        if (eps0 == 0) eps0 = 3.0;
+        if (mu0 == 0) mu0 = 3.0;
+    }
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "lbm_create: out of host memory");
+    c->model = model;
+    c->g = Geometry{nx, ny, nz, (int)n};
+    c->stream = opts ? static_cast<cudaStream_t>(opts->cuda_stream) : nullptr;
+    c->track_rho = (opts && opts->track_rho && model == LBM_MM) ? 1 : 0;
+    c->eps0 = eps0;
+    c->mu0 = mu0;
+    int rc;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, LBM_ECUDA, "lbm_create: no CUDA device");
+    }
+    const size_t pop_bytes = group_bytes(model) * (size_t)n;
+    for (int b = 0; b < 2; ++b) {
+        bool ok = cudaMalloc(&c->buf[b], pop_bytes) == cudaSuccess;
+        if (ok && model == LBM_HV) ok = cudaMalloc(&c->buf2[b], 6 * sizeof(float2) * (size_t)n) == cudaSuccess;
+        if (ok && c->track_rho) ok = cudaMalloc(&c->rho[b], sizeof(float) * (size_t)n) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            release(c);
+            delete c;
+            return fail(nullptr, LBM_ENOMEM, "lbm_create: cannot allocate populations for %lld cells", (long long)n);
+        }
+    }
+    if (c->track_rho && cudaMalloc(&c->rest1, sizeof(float) * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        release(c);
+        delete c;
+        return fail(nullptr, LBM_ENOMEM, "lbm_create: cannot allocate rest populations");
+    }
+    if ((rc = setup_media(c, media)) != LBM_OK) {
+        g_create_error = c->err;
+        release(c);
+        delete c;
+        return rc;
+    }
+    c->reduce_blocks = std::max(1, std::min((int)((n + kBlock - 1) / kBlock), 152 * 4));
+    if (cudaMalloc(&c->d_result, sizeof(double) * 3) != cudaSuccess) {
+        cudaGetLastError();
+        release(c);
+        delete c;
+        return fail(nullptr, LBM_ENOMEM, "lbm_create: cannot allocate reduction result");
+    }
+    bool zero_ok = true;
+    for (int b = 0; b < 2; ++b) {
+        zero_ok &= cudaMemsetAsync(c->buf[b], 0, pop_bytes, c->stream) == cudaSuccess;
+        if (c->buf2[b]) zero_ok &= cudaMemsetAsync(c->buf2[b], 0, 6 * sizeof(float2) * (size_t)n, c->stream) == cudaSuccess;
+        if (c->rho[b]) zero_ok &= cudaMemsetAsync(c->rho[b], 0, sizeof(float) * (size_t)n, c->stream) == cudaSuccess;
+    }
+    if (c->rest1) zero_ok &= cudaMemsetAsync(c->rest1, 0, sizeof(float) * (size_t)n, c->stream) == cudaSuccess;
+    if (!zero_ok) {
+        cudaError_t e = cudaGetLastError();
+        release(c);
+        delete c;
+        return fail(nullptr, LBM_ECUDA, "lbm_create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* ctx) {
+    if (!ctx) return LBM_OK;
+    ensure_device(ctx);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    release(ctx);
+    delete ctx;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* ctx, const float* E, const float* B, int on_device) {
+    if (!ctx) return LBM_EINVAL;
+    if (!E || !B) return fail(ctx, LBM_EINVAL, "lbm_init_fields: E and B are required");
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    const size_t cnt = 3 * (size_t)ctx->g.n;
+    float *dE = nullptr, *dB = nullptr;
+    bool oE = false, oB = false;
+    if ((rc = stage_input(ctx, E, on_device, cnt, &dE, &oE)) != LBM_OK) return rc;
+    if ((rc = stage_input(ctx, B, on_device, cnt, &dB, &oB)) != LBM_OK) {
+        if (oE) cudaFree(dE);
+        return rc;
+    }
+    StepArgs a = base_args(ctx);
+    ctx->cur = 0;
+    bind_buffers(ctx, a, 1, 0);
+    const int launched = ctx->model == LBM_MM ? mm_launch_init(a, dE, dB, ctx->stream) : hv_launch_init(a, dE, dB, ctx->stream);
+    rc = check_launch(ctx, launched);
+    if (rc == LBM_OK && ctx->rho[0]) {
+        if (cudaMemsetAsync(ctx->rho[0], 0, sizeof(float) * ctx->g.n, ctx->stream) != cudaSuccess ||
+            cudaMemsetAsync(ctx->rest1, 0, sizeof(float) * ctx->g.n, ctx->stream) != cudaSuccess)
+            rc = fail(ctx, LBM_ECUDA, "lbm_init_fields: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (oE || oB) {
+        cudaStreamSynchronize(ctx->stream);
+        if (oE) cudaFree(dE);
+        if (oB) cudaFree(dB);
+    }
+    ctx->t = 0;
+    return rc;
+}
+
+int lbm_set_source(lbm_ctx* ctx, const lbm_source* src) {
+    if (!ctx) return LBM_EINVAL;
+    if (!src) return fail(ctx, LBM_EINVAL, "lbm_set_source: src is NULL");
+    if ((int)ctx->sources.size() >= LBM_MAX_SOURCES)
+        return fail(ctx, LBM_EINVAL, "lbm_set_source: at most %d sources", LBM_MAX_SOURCES);
+    if (src->kind != LBM_SRC_CURRENT && src->kind != LBM_SRC_IMPOSE)
+        return fail(ctx, LBM_EINVAL, "lbm_set_source: unknown kind %d", src->kind);
+    if (src->n_cells < 0 || (src->n_cells > 0 && !src->cells))
+        return fail(ctx, LBM_EINVAL, "lbm_set_source: bad cell list");
+    if (src->kind == LBM_SRC_CURRENT && src->n_cells > 0 && !src->w)
+        return fail(ctx, LBM_EINVAL, "lbm_set_source: a current source needs weights");
+    const lbm_time_fn& fn = src->fn;
+    if (fn.kind != LBM_FN_SIN && fn.kind != LBM_FN_TABLE && fn.kind != LBM_FN_CONST)
+        return fail(ctx, LBM_EINVAL, "lbm_set_source: unknown time function %d", fn.kind);
+    if (fn.kind == LBM_FN_SIN && !(fn.period != 0.0 && std::isfinite(fn.period)))
+        return fail(ctx, LBM_EINVAL, "lbm_set_source: sin period must be finite and non-zero");
+    if (fn.kind == LBM_FN_TABLE && (fn.table_len < 0 || (fn.table_len > 0 && !fn.table)))
+        return fail(ctx, LBM_EINVAL, "lbm_set_source: bad table");
+    HostSource s;
+    s.kind = src->kind;
+    s.cells.resize((size_t)src->n_cells);
+    for (int64_t m = 0; m < src->n_cells; ++m) {
+        if (src->cells[m] < 0 || src->cells[m] >= ctx->g.n)
+            return fail(ctx, LBM_EINVAL, "lbm_set_source: cell %lld out of range", (long long)src->cells[m]);
+        s.cells[(size_t)m] = (int)src->cells[m];
+    }
+    if (src->kind == LBM_SRC_CURRENT) s.w.assign(src->w, src->w + 3 * src->n_cells);
+    for (int q = 0; q < 3; ++q) {
+        s.E0[q] = src->kind == LBM_SRC_IMPOSE ? src->E0[q] : 0.f;
+        s.B0[q] = src->kind == LBM_SRC_IMPOSE ? src->B0[q] : 0.f;
+    }
+    s.fn = fn;
+    s.fn.table = nullptr;
+    if (fn.kind == LBM_FN_TABLE && fn.table_len > 0) s.table.assign(fn.table, fn.table + fn.table_len);
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    CUDA_TRY(ctx, ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
+    ctx->sources.push_back(std::move(s));
+    rc = rebuild_sources(ctx);
+    if (rc != LBM_OK) ctx->sources.pop_back();
+    return rc;
+}
+
+int lbm_clear_sources(lbm_ctx* ctx) {
+    if (!ctx) return LBM_EINVAL;
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    CUDA_TRY(ctx, ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
+    ctx->sources.clear();
+    free_sources_device(ctx);
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* ctx, int n) {
+    if (!ctx) return LBM_EINVAL;
+    if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n must be >= 0");
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    StepArgs a = base_args(ctx);
+    for (int s = 0; s < n; ++s) {
+        const int in = ctx->cur, out = 1 - ctx->cur;
+        bind_buffers(ctx, a, in, out);
+        fill_scalars(ctx, a, ctx->t + 1);
+        const int launched = ctx->model == LBM_MM ? mm_launch_step(a, ctx->stream) : hv_launch_step(a, ctx->stream);
+        if ((rc = check_launch(ctx, launched)) != LBM_OK) return rc;
+        ctx->cur = out;
+        ctx->t += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_fields(lbm_ctx* ctx, unsigned mask, float* out, int on_device) {
+    if (!ctx) return LBM_EINVAL;
+    if (!out) return fail(ctx, LBM_EINVAL, "lbm_fields: out is NULL");
+    if (mask == 0 || (mask & ~31u)) return fail(ctx, LBM_EINVAL, "lbm_fields: bad mask 0x%x", mask);
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    int nf = 0;
+    for (int b = 0; b < 5; ++b) nf += (mask >> b) & 1;
+    const size_t cnt = 3 * (size_t)ctx->g.n * nf;
+    float* dev = out;
+    if (!on_device) {
+        if (cudaMalloc(&dev, sizeof(float) * cnt) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, LBM_ENOMEM, "lbm_fields: cannot allocate %zu floats", cnt);
+        }
+    }
+    FieldsOut fo{nullptr, nullptr, nullptr, nullptr, nullptr};
+    float** slots[5] = {&fo.E, &fo.B, &fo.D, &fo.H, &fo.J};
+    size_t off = 0;
+    for (int b = 0; b < 5; ++b)
+        if ((mask >> b) & 1) {
+            *slots[b] = dev + off;
+            off += 3 * (size_t)ctx->g.n;
+        }
+    StepArgs a = base_args(ctx);
+    bind_buffers(ctx, a, ctx->cur, 1 - ctx->cur);
+    fill_scalars(ctx, a, ctx->t + 1);
+    const int launched = ctx->model == LBM_MM ? mm_launch_fields(a, fo, ctx->stream) : hv_launch_fields(a, fo, ctx->stream);
+    rc = check_launch(ctx, launched);
+    if (!on_device) {
+        if (rc == LBM_OK && cudaMemcpyAsync(out, dev, sizeof(float) * cnt, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+            rc = fail(ctx, LBM_ECUDA, "lbm_fields: copy: %s", cudaGetErrorString(cudaGetLastError()));
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == LBM_OK)
+            rc = fail(ctx, LBM_ECUDA, "lbm_fields: %s", cudaGetErrorString(cudaGetLastError()));
+        cudaFree(dev);
+    }
+    return rc;
+}
+
+int lbm_get_populations(lbm_ctx* ctx, float* out, int on_device) {
+    if (!ctx) return LBM_EINVAL;
+    if (!out) return fail(ctx, LBM_EINVAL, "lbm_get_populations: out is NULL");
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    const size_t cnt = (size_t)lbm_num_populations(ctx->model) * ctx->g.n;
+    float* dev = out;
+    if (!on_device && cudaMalloc(&dev, sizeof(float) * cnt) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LBM_ENOMEM, "lbm_get_populations: cannot allocate %zu floats", cnt);
+    }
+    StepArgs a = base_args(ctx);
+    bind_buffers(ctx, a, ctx->cur, 1 - ctx->cur);
+    const int launched = ctx->model == LBM_MM ? mm_launch_get(a, dev, ctx->stream) : hv_launch_get(a, dev, ctx->stream);
+    rc = check_launch(ctx, launched);
+    if (!on_device) {
+        if (rc == LBM_OK && cudaMemcpyAsync(out, dev, sizeof(float) * cnt, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+            rc = fail(ctx, LBM_ECUDA, "lbm_get_populations: copy: %s", cudaGetErrorString(cudaGetLastError()));
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == LBM_OK)
+            rc = fail(ctx, LBM_ECUDA, "lbm_get_populations: %s", cudaGetErrorString(cudaGetLastError()));
+        cudaFree(dev);
+    }
+    return rc;
+}
+
+int lbm_set_populations(lbm_ctx* ctx, const float* in, int on_device, int64_t t) {
+    if (!ctx) return LBM_EINVAL;
+    if (!in) return fail(ctx, LBM_EINVAL, "lbm_set_populations: in is NULL");
+    if (t < 0) return fail(ctx, LBM_EINVAL, "lbm_set_populations: t must be >= 0");
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    const size_t cnt = (size_t)lbm_num_populations(ctx->model) * ctx->g.n;
+    float* dev = nullptr;
+    bool owned = false;
+    if ((rc = stage_input(ctx, in, on_device, cnt, &dev, &owned)) != LBM_OK) return rc;
+    StepArgs a = base_args(ctx);
+    ctx->cur = 0;
+    bind_buffers(ctx, a, 1, 0);
+    const int launched = ctx->model == LBM_MM ? mm_launch_set(a, dev, ctx->stream) : hv_launch_set(a, dev, ctx->stream);
+    rc = check_launch(ctx, launched);
+    if (owned) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(dev);
+    }
+    ctx->t = t;
+    return rc;
+}
+
+int lbm_reduce(lbm_ctx* ctx, double out[3]) {
+    if (!ctx) return LBM_EINVAL;
+    if (!out) return fail(ctx, LBM_EINVAL, "lbm_reduce: out is NULL");
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    const int ns_blocks = ctx->n_special > 0 ? (ctx->n_special + kBlock - 1) / kBlock : 0;
+    if ((rc = ensure_partials(ctx, ctx->reduce_blocks + ns_blocks)) != LBM_OK) return rc;
+    StepArgs a = base_args(ctx);
+    bind_buffers(ctx, a, ctx->cur, 1 - ctx->cur);
+    fill_scalars(ctx, a, ctx->t + 1);
+    const int launched = ctx->model == LBM_MM
+                             ? mm_launch_reduce(a, ctx->d_partials, ctx->reduce_blocks, ctx->d_result, ctx->stream)
+                             : hv_launch_reduce(a, ctx->d_partials, ctx->reduce_blocks, ctx->d_result, ctx->stream);
+    if ((rc = check_launch(ctx, launched)) != LBM_OK) return rc;
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->d_result, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+int lbm_check_finite(lbm_ctx* ctx) {
+    double r[3];
+    int rc = lbm_reduce(ctx, r);
+    if (rc != LBM_OK) return rc;
+    if (!std::isfinite(r[1])) return fail(ctx, LBM_ENONFINITE, "non-finite population (sum of squares %g)", r[1]);
+    return LBM_OK;
+}
+
+int64_t lbm_time(const lbm_ctx* ctx) { return ctx ? ctx->t : -1; }
+int64_t lbm_launch_count(const lbm_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int lbm_sync(lbm_ctx* ctx) {
+    if (!ctx) return LBM_EINVAL;
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// Deterministic final reduction: one block, each thread sums a fixed strided subset in order.
+namespace lbm {
+namespace {
+__global__ void __launch_bounds__(kBlock) reduce_partials_kernel(const double* __restrict__ p, int nb,
+                                                                 double* __restrict__ result) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kBlock) {
+        s0 += p[3 * b];
+        s1 += p[3 * b + 1];
+        s2 += p[3 * b + 2];
+    }
+    block_sum3_store(s0, s1, s2, result);
+}
+}  // namespace
+
+int launch_reduce_partials(const double* partials, int n_blocks, double* result, cudaStream_t st) {
+    reduce_partials_kernel<<<1, kBlock, 0, st>>>(partials, n_blocks, result);
+    return 1;
+}
+}  // namespace lbm

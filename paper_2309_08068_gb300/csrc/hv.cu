@@ -1,0 +1,336 @@
+// Modified Hauser-Verhey (HV) model kernels, arXiv 2309.08068 Section III.
+//
+// One thread updates one cell: 6 directions, each an electric vector e_i and a magnetic vector h_i
+// (36 scalars), pulled as a float4 (e_x, e_y, e_z, h_x) and a float2 (h_y, h_z) from cell x - v_i.
+// Velocities in the Section III order: v1 = +x, v2 = +y, v3 = -x, v4 = -y, v5 = -z, v6 = +z.
+//
+// With tau = 1/2 the collision (eqs. equilibriumHV, CollisionHV, CollisionmodifiedHV) is
+//   e_i' = 2 e_i^eq - e_i + T_i = D/3 - v_i x H - e_i - (J . v_i) v_i / 2
+//   h_i' = 2 h_i^eq - h_i       = B/3 + v_i x E - h_i
+// with D = sum e_i, B = sum h_i (eq. MacroscopicFieldsHV), E = D / eps, H = B / mu, eps = eps0 eps_r,
+// mu = mu0 mu_r, and J = sigma E + J_ext. For v_i = s a (a a unit axis, s = +-1) the source term is
+// -(J_a / 2) a whatever the sign s.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+// Axis (0, 1, 2) and sign of v_i, i = 1..6.
+constexpr int kHVAxis[6] = {0, 1, 0, 1, 2, 2};
+constexpr int kHVSign[6] = {1, 1, -1, -1, -1, 1};
+
+// s * (a x X) for the unit axis a.
+template <int A, int S>
+__device__ __forceinline__ float3 axis_cross(float3 X) {
+    float3 r;
+    if constexpr (A == 0) r = make_float3(0.f, -X.z, X.y);
+    else if constexpr (A == 1) r = make_float3(X.z, 0.f, -X.x);
+    else r = make_float3(-X.y, X.x, 0.f);
+    if constexpr (S < 0) r = make_float3(-r.x, -r.y, -r.z);
+    return r;
+}
+
+// Offset of the cell x - v_i.
+template <int I>
+__device__ __forceinline__ int pull_index(const Neighbourhood& h) {
+    constexpr int a = kHVAxis[I], s = kHVSign[I];
+    return shifted<a == 0 ? -s : 0, a == 1 ? -s : 0, a == 2 ? -s : 0>(h);
+}
+
+// Offset of the cell x + v_i.
+template <int I>
+__device__ __forceinline__ int push_index(const Neighbourhood& h) {
+    constexpr int a = kHVAxis[I], s = kHVSign[I];
+    return shifted<a == 0 ? s : 0, a == 1 ? s : 0, a == 2 ? s : 0>(h);
+}
+
+__device__ __forceinline__ void hv_pull(const float4* __restrict__ ein, const float2* __restrict__ hin, int n,
+                                        const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) {
+    static_for<0, 6>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const int src = pull_index<i>(h);
+        e[i] = __ldg(ein + (size_t)i * n + src);
+        hy[i] = __ldg(hin + (size_t)i * n + src);
+    });
+}
+
+struct HVFields {
+    float3 D, B, E, H, J;
+};
+
+__device__ __forceinline__ HVFields hv_fields(const float4 (&e)[6], const float2 (&hy)[6], float3 mat, float eps0,
+                                              float mu0, float3 jext) {
+    HVFields F;
+    // Pairwise sums ((1 + 2) + (3 + 4)) + (5 + 6) over the directions.
+    float tx[6], ty[6], tz[6], ux[6], uy[6], uz[6];
+    static_for<0, 6>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        tx[i] = e[i].x;
+        ty[i] = e[i].y;
+        tz[i] = e[i].z;
+        ux[i] = e[i].w;
+        uy[i] = hy[i].x;
+        uz[i] = hy[i].y;
+    });
+    const float dx = pairwise_sum<0, 4>(tx) + pairwise_sum<4, 6>(tx);
+    const float dy = pairwise_sum<0, 4>(ty) + pairwise_sum<4, 6>(ty);
+    const float dz = pairwise_sum<0, 4>(tz) + pairwise_sum<4, 6>(tz);
+    const float bx = pairwise_sum<0, 4>(ux) + pairwise_sum<4, 6>(ux);
+    const float by = pairwise_sum<0, 4>(uy) + pairwise_sum<4, 6>(uy);
+    const float bz = pairwise_sum<0, 4>(uz) + pairwise_sum<4, 6>(uz);
+    const float eps = eps0 * mat.x, mu = mu0 * mat.y;
+    F.D = make_float3(dx, dy, dz);
+    F.B = make_float3(bx, by, bz);
+    F.E = make_float3(dx / eps, dy / eps, dz / eps);
+    F.H = make_float3(bx / mu, by / mu, bz / mu);
+    F.J = make_float3(mat.z * F.E.x + jext.x, mat.z * F.E.y + jext.y, mat.z * F.E.z + jext.z);
+    return F;
+}
+
+template <int M, bool kSpecial>
+__global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
+    int i, m = 0;
+    if constexpr (kSpecial) {
+        m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        i = a.sv.cell[m];
+    } else {
+        i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+    }
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, i);
+    float4 e[6];
+    float2 hy[6];
+    hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
+    const float3 mat = load_material<M>(a.media, i);
+    CellSource cs;
+    float3 jext = make_float3(0.f, 0.f, 0.f);
+    if constexpr (kSpecial) {
+        cs = cell_source(a.sv, a.sc, m);
+        jext = cs.J;
+    }
+    const HVFields F = hv_fields(e, hy, mat, a.eps0, a.mu0, jext);
+    const float3 q = make_float3(F.D.x / 3.f, F.D.y / 3.f, F.D.z / 3.f);
+    const float3 p = make_float3(F.B.x / 3.f, F.B.y / 3.f, F.B.z / 3.f);
+    float4* __restrict__ eout = static_cast<float4*>(a.fout);
+    float2* __restrict__ hout = static_cast<float2*>(a.fout2);
+    static_for<0, 6>([&](auto ic) {
+        constexpr int k = decltype(ic)::value;
+        constexpr int A = kHVAxis[k], S = kHVSign[k];
+        const float3 vH = axis_cross<A, S>(F.H);
+        const float3 vE = axis_cross<A, S>(F.E);
+        float3 eo = make_float3(q.x - vH.x - e[k].x, q.y - vH.y - e[k].y, q.z - vH.z - e[k].z);
+        // eq. SourceTermHV: T_i = -(J . v_i) v_i / 2 = -(J_A / 2) along axis A.
+        if constexpr (A == 0) eo.x -= 0.5f * F.J.x;
+        else if constexpr (A == 1) eo.y -= 0.5f * F.J.y;
+        else eo.z -= 0.5f * F.J.z;
+        float3 ho = make_float3(p.x + vE.x - e[k].w, p.y + vE.y - hy[k].x, p.z + vE.z - hy[k].y);
+        if constexpr (kSpecial) {
+            if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
+                const float eps = a.eps0 * mat.x, mu = a.mu0 * mat.y;
+                const float3 Hi = make_float3(cs.B.x / mu, cs.B.y / mu, cs.B.z / mu);
+                const float3 cH = axis_cross<A, S>(Hi);
+                const float3 cE = axis_cross<A, S>(cs.E);
+                eo = make_float3((eps * cs.E.x) / 6.f - 0.5f * cH.x, (eps * cs.E.y) / 6.f - 0.5f * cH.y,
+                                 (eps * cs.E.z) / 6.f - 0.5f * cH.z);
+                ho = make_float3(cs.B.x / 6.f + 0.5f * cE.x, cs.B.y / 6.f + 0.5f * cE.y, cs.B.z / 6.f + 0.5f * cE.z);
+            }
+        }
+        eout[(size_t)k * n + i] = make_float4(eo.x, eo.y, eo.z, ho.x);
+        hout[(size_t)k * n + i] = make_float2(ho.y, ho.z);
+    });
+}
+
+// Equilibria for fields E, B and J = 0 (Appendix B initialisation), stored so that cell x pulls
+// them at the next step: direction i at y holds the equilibrium of cell y + v_i.
+template <int M>
+__global__ void __launch_bounds__(kBlock) hv_init_kernel(StepArgs a, const float* __restrict__ E,
+                                                         const float* __restrict__ B) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= a.g.n) return;
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, y);
+    float4* __restrict__ eout = static_cast<float4*>(a.fout);
+    float2* __restrict__ hout = static_cast<float2*>(a.fout2);
+    static_for<0, 6>([&](auto ic) {
+        constexpr int k = decltype(ic)::value;
+        constexpr int A = kHVAxis[k], S = kHVSign[k];
+        const int x = push_index<k>(h);
+        const float3 mat = load_material<M>(a.media, x);
+        const float eps = a.eps0 * mat.x, mu = a.mu0 * mat.y;
+        const float3 Ex = make_float3(__ldg(&E[x]), __ldg(&E[n + x]), __ldg(&E[2 * n + x]));
+        const float3 Bx = make_float3(__ldg(&B[x]), __ldg(&B[n + x]), __ldg(&B[2 * n + x]));
+        const float3 Hx = make_float3(Bx.x / mu, Bx.y / mu, Bx.z / mu);
+        const float3 cH = axis_cross<A, S>(Hx);
+        const float3 cE = axis_cross<A, S>(Ex);
+        // e^eq = (D - 3 v x B / mu) / 6 = D/6 - (v x H)/2;  h^eq = (B + 3 v x D / eps) / 6 = B/6 + (v x E)/2
+        eout[(size_t)k * n + y] = make_float4((eps * Ex.x) / 6.f - 0.5f * cH.x, (eps * Ex.y) / 6.f - 0.5f * cH.y,
+                                              (eps * Ex.z) / 6.f - 0.5f * cH.z, Bx.x / 6.f + 0.5f * cE.x);
+        hout[(size_t)k * n + y] = make_float2(Bx.y / 6.f + 0.5f * cE.y, Bx.z / 6.f + 0.5f * cE.z);
+    });
+}
+
+template <int M, bool kSpecial>
+__global__ void __launch_bounds__(kBlock) hv_fields_kernel(StepArgs a, FieldsOut out) {
+    int i, m = 0;
+    if constexpr (kSpecial) {
+        m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        i = a.sv.cell[m];
+    } else {
+        i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+    }
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, i);
+    float4 e[6];
+    float2 hy[6];
+    hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
+    const float3 mat = load_material<M>(a.media, i);
+    float3 jext = make_float3(0.f, 0.f, 0.f);
+    if constexpr (kSpecial) jext = cell_source(a.sv, a.sc, m).J;
+    const HVFields F = hv_fields(e, hy, mat, a.eps0, a.mu0, jext);
+    auto put = [&](float* p, float3 v) {
+        if (p) {
+            p[i] = v.x;
+            p[n + i] = v.y;
+            p[2 * n + i] = v.z;
+        }
+    };
+    put(out.E, F.E);
+    put(out.B, F.B);
+    put(out.D, F.D);
+    put(out.H, F.H);
+    put(out.J, F.J);
+}
+
+// Canonical layout out[k * n + x], k = r*18 + (i-1)*3 + c.
+__global__ void __launch_bounds__(kBlock) hv_get_kernel(StepArgs a, float* __restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.g.n) return;
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, x);
+    float4 e[6];
+    float2 hy[6];
+    hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
+    static_for<0, 6>([&](auto ic) {
+        constexpr int k = decltype(ic)::value;
+        out[(size_t)(3 * k + 0) * n + x] = e[k].x;
+        out[(size_t)(3 * k + 1) * n + x] = e[k].y;
+        out[(size_t)(3 * k + 2) * n + x] = e[k].z;
+        out[(size_t)(18 + 3 * k + 0) * n + x] = e[k].w;
+        out[(size_t)(18 + 3 * k + 1) * n + x] = hy[k].x;
+        out[(size_t)(18 + 3 * k + 2) * n + x] = hy[k].y;
+    });
+}
+
+__global__ void __launch_bounds__(kBlock) hv_set_kernel(StepArgs a, const float* __restrict__ in) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= a.g.n) return;
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, y);
+    float4* __restrict__ eout = static_cast<float4*>(a.fout);
+    float2* __restrict__ hout = static_cast<float2*>(a.fout2);
+    static_for<0, 6>([&](auto ic) {
+        constexpr int k = decltype(ic)::value;
+        const int x = push_index<k>(h);
+        eout[(size_t)k * n + y] = make_float4(in[(size_t)(3 * k) * n + x], in[(size_t)(3 * k + 1) * n + x],
+                                              in[(size_t)(3 * k + 2) * n + x], in[(size_t)(18 + 3 * k) * n + x]);
+        hout[(size_t)k * n + y] = make_float2(in[(size_t)(19 + 3 * k) * n + x], in[(size_t)(20 + 3 * k) * n + x]);
+    });
+}
+
+// Per-block partial sums of (1/2)(E.D + B.H) and sum f^2 (E does not depend on J_ext in HV, so no
+// source-cell correction is needed).
+template <int M>
+__global__ void __launch_bounds__(kBlock) hv_reduce_kernel(StepArgs a, double* __restrict__ partials) {
+    double w = 0.0, f2 = 0.0;
+    const int n = a.g.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Neighbourhood h = neighbourhood(a.g, i);
+        float4 e[6];
+        float2 hy[6];
+        hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
+        const float3 mat = load_material<M>(a.media, i);
+        const HVFields F = hv_fields(e, hy, mat, a.eps0, a.mu0, make_float3(0.f, 0.f, 0.f));
+        w += 0.5 * ((double)F.E.x * F.D.x + (double)F.E.y * F.D.y + (double)F.E.z * F.D.z +
+                    (double)F.B.x * F.H.x + (double)F.B.y * F.H.y + (double)F.B.z * F.H.z);
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            s += (double)e[k].x * e[k].x + (double)e[k].y * e[k].y + (double)e[k].z * e[k].z +
+                 (double)e[k].w * e[k].w + (double)hy[k].x * hy[k].x + (double)hy[k].y * hy[k].y;
+        f2 += s;
+    }
+    block_sum3_store(w, f2, 0.0, partials + 3 * blockIdx.x);
+}
+
+inline int blocks_for(int n) { return (n + kBlock - 1) / kBlock; }
+
+}  // namespace
+
+int hv_launch_step(const StepArgs& a, cudaStream_t st) {
+    const int nb = blocks_for(a.g.n);
+    switch (a.media_mode) {
+        case kUniform: hv_step_kernel<kUniform, false><<<nb, kBlock, 0, st>>>(a); break;
+        case kTable: hv_step_kernel<kTable, false><<<nb, kBlock, 0, st>>>(a); break;
+        default: hv_step_kernel<kPerCell, false><<<nb, kBlock, 0, st>>>(a); break;
+    }
+    if (a.sv.n_special == 0) return 1;
+    const int ns = blocks_for(a.sv.n_special);
+    switch (a.media_mode) {
+        case kUniform: hv_step_kernel<kUniform, true><<<ns, kBlock, 0, st>>>(a); break;
+        case kTable: hv_step_kernel<kTable, true><<<ns, kBlock, 0, st>>>(a); break;
+        default: hv_step_kernel<kPerCell, true><<<ns, kBlock, 0, st>>>(a); break;
+    }
+    return 2;
+}
+
+int hv_launch_init(const StepArgs& a, const float* E, const float* B, cudaStream_t st) {
+    const int nb = blocks_for(a.g.n);
+    switch (a.media_mode) {
+        case kUniform: hv_init_kernel<kUniform><<<nb, kBlock, 0, st>>>(a, E, B); break;
+        case kTable: hv_init_kernel<kTable><<<nb, kBlock, 0, st>>>(a, E, B); break;
+        default: hv_init_kernel<kPerCell><<<nb, kBlock, 0, st>>>(a, E, B); break;
+    }
+    return 1;
+}
+
+int hv_launch_fields(const StepArgs& a, FieldsOut out, cudaStream_t st) {
+    const int nb = blocks_for(a.g.n);
+    switch (a.media_mode) {
+        case kUniform: hv_fields_kernel<kUniform, false><<<nb, kBlock, 0, st>>>(a, out); break;
+        case kTable: hv_fields_kernel<kTable, false><<<nb, kBlock, 0, st>>>(a, out); break;
+        default: hv_fields_kernel<kPerCell, false><<<nb, kBlock, 0, st>>>(a, out); break;
+    }
+    if (a.sv.n_special == 0) return 1;
+    const int ns = blocks_for(a.sv.n_special);
+    switch (a.media_mode) {
+        case kUniform: hv_fields_kernel<kUniform, true><<<ns, kBlock, 0, st>>>(a, out); break;
+        case kTable: hv_fields_kernel<kTable, true><<<ns, kBlock, 0, st>>>(a, out); break;
+        default: hv_fields_kernel<kPerCell, true><<<ns, kBlock, 0, st>>>(a, out); break;
+    }
+    return 2;
+}
+
+int hv_launch_get(const StepArgs& a, float* out, cudaStream_t st) {
+    hv_get_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, out);
+    return 1;
+}
+
+int hv_launch_set(const StepArgs& a, const float* in, cudaStream_t st) {
+    hv_set_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, in);
+    return 1;
+}
+
+int hv_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* result, cudaStream_t st) {
+    switch (a.media_mode) {
+        case kUniform: hv_reduce_kernel<kUniform><<<n_blocks, kBlock, 0, st>>>(a, partials); break;
+        case kTable: hv_reduce_kernel<kTable><<<n_blocks, kBlock, 0, st>>>(a, partials); break;
+        default: hv_reduce_kernel<kPerCell><<<n_blocks, kBlock, 0, st>>>(a, partials); break;
+    }
+    return 1 + launch_reduce_partials(partials, n_blocks, result, st);
+}
+
+}  // namespace lbm

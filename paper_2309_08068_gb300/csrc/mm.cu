@@ -1,0 +1,425 @@
+// Mendoza-Munoz (MM) model kernels, arXiv 2309.08068 Section II.
+//
+// One thread updates one cell. The 48 moving populations arrive as 12 float4 pulls (one per
+// D3Q13 velocity; the four values of a velocity move together), the whole collision runs in
+// registers, and the 12 float4 results are stored at the cell (pull scheme). Sources and imposed
+// cells are handled by a second, small launch over the merged source-cell list that recomputes
+// those cells with their current and imposed fields and overwrites them; the main launch stays
+// branch-free.
+//
+// Direction tables. Direction d = p*4 + (i-1) with the plane p and index i of eq.
+// VelocitySetMiller: v_i^p = sqrt(2) (cos((2i-1) pi/4), sin((2i-1) pi/4)) in the xy (p = 0), xz
+// (p = 1) and yz (p = 2) planes, which are the edge diagonals below. The electric vectors of eq.
+// ElectromagneticVectorsMiller are e_{i0} = v_{[(i+2) mod 4]+1} / 2 and e_{i1} = v_{[i mod 4]+1} / 2
+// = -e_{i0}; kMMEh holds 2 e_{i0}. The magnetic vectors b_{ij} = v_i x e_{ij} come out as -z for
+// every direction of plane 0, +y for plane 1 and -x for plane 2, with b_{i1} = -b_{i0}.
+//
+// Because e_{i1} = -e_{i0} and b_{i1} = -b_{i0}, only the differences f_{d0} - f_{d1} enter the
+// moments D' and B; the sums enter only rho_c. The collision below is written per velocity in
+// terms of s = v.J/16, alpha = (eps_r/4) E.e0 + B.b0/(8 mu_r) and beta = E.e0/4 + B.b0/8:
+//   f^(0)eq_{d0,d1} = s +- alpha,  f^(1)eq_{d0,d1} = s +- beta   (eq. equilibriumsMiller)
+//   f' = 2 f^eq - f                                              (eq. CollisionMiller)
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kMMV[12][3] = {{1, 1, 0},  {-1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                             {1, 0, 1},  {-1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                             {0, 1, 1},  {0, -1, 1},  {0, -1, -1}, {0, 1, -1}};
+constexpr int kMMEh[12][3] = {{1, -1, 0}, {1, 1, 0},  {-1, 1, 0}, {-1, -1, 0},
+                              {1, 0, -1}, {1, 0, 1},  {-1, 0, 1}, {-1, 0, -1},
+                              {0, 1, -1}, {0, 1, 1},  {0, -1, 1}, {0, -1, -1}};
+constexpr int kMMB[12][3] = {{0, 0, -1}, {0, 0, -1}, {0, 0, -1}, {0, 0, -1},
+                             {0, 1, 0},  {0, 1, 0},  {0, 1, 0},  {0, 1, 0},
+                             {-1, 0, 0}, {-1, 0, 0}, {-1, 0, 0}, {-1, 0, 0}};
+
+// Dot product of a compile-time {-1,0,1} vector row with (x, y, z).
+template <int A, int B, int C>
+__device__ __forceinline__ float sdot(float x, float y, float z) {
+    float s = 0.f;
+    acc<A>(s, x);
+    acc<B>(s, y);
+    acc<C>(s, z);
+    return s;
+}
+
+struct MMFields {
+    float3 Dpp;  // eps_r E = D (physical displacement, eps0 = 1)
+    float3 E;
+    float3 B;
+    float3 J;
+    float rho;
+    float inv4mu;  // 1 / (4 mu_r)
+};
+
+// Moments of the 48 moving populations (eq. MacroscopicFieldsMiller), then E and J with ohmic
+// conductivity and an external current (eqs. MacroscopicEMiller, MacorscopicCurrentMiller):
+//   eps_r E = (D' - mu0 J_ext / 4) / (1 + mu0 sigma / (4 eps_r)),  J = sigma E + J_ext,  mu0 = 2.
+// Position of direction d among the directions whose row of table T has a non-zero component a.
+template <const int (&T)[12][3]>
+constexpr int rank_in_column(int d, int a) {
+    int r = 0;
+    for (int k = 0; k < d; ++k) r += T[k][a] != 0;
+    return r;
+}
+
+// Signed terms of one moment component, sum_d T[d][a] * x_d, summed pairwise in direction order.
+// Each component of D' has 8 terms (2 e_{i0} has two non-zero entries), each component of B has 4.
+template <const int (&T)[12][3], int A, int N>
+__device__ __forceinline__ float moment_component(const float (&x)[12]) {
+    float t[N];
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        if constexpr (T[d][A] != 0) {
+            constexpr int r = rank_in_column<T>(d, A);
+            if constexpr (T[d][A] > 0) t[r] = x[d];
+            else t[r] = -x[d];
+        }
+    });
+    return pairwise_sum<0, N>(t);
+}
+
+template <bool kRho>
+__device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0, float3 mat, float3 jext) {
+    float de[12], db[12];
+    float rho = rest0;
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        de[d] = f[d].x - f[d].y;
+        db[d] = f[d].z - f[d].w;
+        if constexpr (kRho) rho += f[d].x + f[d].y;
+    });
+    const float dx = moment_component<kMMEh, 0, 8>(de), dy = moment_component<kMMEh, 1, 8>(de),
+                dz = moment_component<kMMEh, 2, 8>(de);
+    const float bx = moment_component<kMMB, 0, 4>(db), by = moment_component<kMMB, 1, 4>(db),
+                bz = moment_component<kMMB, 2, 4>(db);
+    MMFields o;
+    const float g = 1.f / (1.f + 0.5f * (mat.z / mat.x));
+    o.Dpp.x = (0.5f * dx - 0.5f * jext.x) * g;
+    o.Dpp.y = (0.5f * dy - 0.5f * jext.y) * g;
+    o.Dpp.z = (0.5f * dz - 0.5f * jext.z) * g;
+    o.E.x = o.Dpp.x / mat.x;
+    o.E.y = o.Dpp.y / mat.x;
+    o.E.z = o.Dpp.z / mat.x;
+    o.B = make_float3(bx, by, bz);
+    o.J.x = mat.z * o.E.x + jext.x;
+    o.J.y = mat.z * o.E.y + jext.y;
+    o.J.z = mat.z * o.E.z + jext.z;
+    o.rho = rho;
+    o.inv4mu = 0.25f / mat.y;
+    return o;
+}
+
+// Pull the 12 groups of cell i from the previous step's buffer: direction d from cell i - v_d.
+__device__ __forceinline__ void mm_pull(const float4* __restrict__ fin, int n, const Neighbourhood& h,
+                                        float4 (&f)[12]) {
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        const int src = shifted<-kMMV[d][0], -kMMV[d][1], -kMMV[d][2]>(h);
+        f[d] = __ldg(fin + (size_t)d * n + src);
+    });
+}
+
+template <int M, bool kSpecial, bool kRho>
+__global__ void __launch_bounds__(kBlock) mm_step_kernel(StepArgs a) {
+    int i, m = 0;
+    if constexpr (kSpecial) {
+        m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        i = a.sv.cell[m];
+    } else {
+        i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+    }
+    const int n = a.g.n;
+    const float4* __restrict__ fin = static_cast<const float4*>(a.fin);
+    float4* __restrict__ fout = static_cast<float4*>(a.fout);
+    const Neighbourhood h = neighbourhood(a.g, i);
+    float4 f[12];
+    mm_pull(fin, n, h, f);
+    const float3 mat = load_material<M>(a.media, i);
+    float rest0 = 0.f;
+    if constexpr (kRho) rest0 = a.rho_in[i];
+    CellSource cs;
+    float3 jext = make_float3(0.f, 0.f, 0.f);
+    if constexpr (kSpecial) {
+        cs = cell_source(a.sv, a.sc, m);
+        jext = cs.J;
+    }
+    const MMFields F = mm_fields<kRho>(f, rest0, mat, jext);
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        constexpr int v0 = kMMV[d][0], v1 = kMMV[d][1], v2 = kMMV[d][2];
+        constexpr int e0 = kMMEh[d][0], e1 = kMMEh[d][1], e2 = kMMEh[d][2];
+        constexpr int b0 = kMMB[d][0], b1 = kMMB[d][1], b2 = kMMB[d][2];
+        const float two_s = 0.125f * sdot<v0, v1, v2>(F.J.x, F.J.y, F.J.z);
+        const float bb = sdot<b0, b1, b2>(F.B.x, F.B.y, F.B.z);
+        const float two_alpha = 0.25f * sdot<e0, e1, e2>(F.Dpp.x, F.Dpp.y, F.Dpp.z) + bb * F.inv4mu;
+        const float two_beta = 0.25f * sdot<e0, e1, e2>(F.E.x, F.E.y, F.E.z) + 0.25f * bb;
+        float4 o;
+        o.x = two_s + two_alpha - f[d].x;
+        o.y = two_s - two_alpha - f[d].y;
+        o.z = two_s + two_beta - f[d].z;
+        o.w = two_s - two_beta - f[d].w;
+        if constexpr (kSpecial) {
+            if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
+                const float bi = sdot<b0, b1, b2>(cs.B.x, cs.B.y, cs.B.z);
+                const float ee = sdot<e0, e1, e2>(cs.E.x, cs.E.y, cs.E.z);
+                const float alpha = 0.125f * (mat.x * ee) + 0.5f * bi * F.inv4mu;
+                const float beta = 0.125f * ee + 0.125f * bi;
+                o = make_float4(alpha, -alpha, beta, -beta);
+            }
+        }
+        fout[(size_t)d * n + i] = o;
+    });
+    if constexpr (kRho) a.rho_out[i] = 2.f * F.rho - rest0;  // f_0^(0)eq = rho_c; stays in place
+}
+
+// Equilibrium populations of cell x for fields E, B and J = 0 (Appendix B initialisation).
+template <int M>
+__global__ void __launch_bounds__(kBlock) mm_init_kernel(StepArgs a, const float* __restrict__ E,
+                                                         const float* __restrict__ B) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= a.g.n) return;
+    const int n = a.g.n;
+    float4* __restrict__ fout = static_cast<float4*>(a.fout);
+    const Neighbourhood h = neighbourhood(a.g, y);
+    // Stored value at y for direction d is the population cell x = y + v_d pulls next step.
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        constexpr int e0 = kMMEh[d][0], e1 = kMMEh[d][1], e2 = kMMEh[d][2];
+        constexpr int b0 = kMMB[d][0], b1 = kMMB[d][1], b2 = kMMB[d][2];
+        const int x = shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h);
+        const float3 mat = load_material<M>(a.media, x);
+        const float ee = sdot<e0, e1, e2>(__ldg(&E[x]), __ldg(&E[n + x]), __ldg(&E[2 * n + x]));
+        const float bb = sdot<b0, b1, b2>(__ldg(&B[x]), __ldg(&B[n + x]), __ldg(&B[2 * n + x]));
+        const float alpha = 0.125f * (mat.x * ee) + bb * (0.125f / mat.y);
+        const float beta = 0.125f * ee + 0.125f * bb;
+        fout[(size_t)d * n + y] = make_float4(alpha, -alpha, beta, -beta);
+    });
+}
+
+template <int M, bool kSpecial, bool kRho>
+__global__ void __launch_bounds__(kBlock) mm_fields_kernel(StepArgs a, FieldsOut out) {
+    int i, m = 0;
+    if constexpr (kSpecial) {
+        m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        i = a.sv.cell[m];
+    } else {
+        i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+    }
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, i);
+    float4 f[12];
+    mm_pull(static_cast<const float4*>(a.fin), n, h, f);
+    const float3 mat = load_material<M>(a.media, i);
+    float3 jext = make_float3(0.f, 0.f, 0.f);
+    if constexpr (kSpecial) jext = cell_source(a.sv, a.sc, m).J;
+    const MMFields F = mm_fields<false>(f, 0.f, mat, jext);
+    auto put = [&](float* p, float3 v) {
+        if (p) {
+            p[i] = v.x;
+            p[n + i] = v.y;
+            p[2 * n + i] = v.z;
+        }
+    };
+    put(out.E, F.E);
+    put(out.B, F.B);
+    put(out.D, F.Dpp);  // D = eps0 eps_r E with eps0 = 1
+    const float inv2mu = 1.f / (2.f * mat.y);  // H = B / (mu0 mu_r), mu0 = 2
+    put(out.H, make_float3(F.B.x * inv2mu, F.B.y * inv2mu, F.B.z * inv2mu));
+    put(out.J, F.J);
+}
+
+// Canonical layout out[k * n + x]: k = r*24 + p*8 + (i-1)*2 + j = r*24 + 2d + j; 48, 49 rest.
+__global__ void __launch_bounds__(kBlock) mm_get_kernel(StepArgs a, const float* __restrict__ rest1,
+                                                        float* __restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.g.n) return;
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, x);
+    float4 f[12];
+    mm_pull(static_cast<const float4*>(a.fin), n, h, f);
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        out[(size_t)(2 * d) * n + x] = f[d].x;
+        out[(size_t)(2 * d + 1) * n + x] = f[d].y;
+        out[(size_t)(24 + 2 * d) * n + x] = f[d].z;
+        out[(size_t)(25 + 2 * d) * n + x] = f[d].w;
+    });
+    out[(size_t)48 * n + x] = a.rho_in ? a.rho_in[x] : 0.f;
+    out[(size_t)49 * n + x] = rest1 ? rest1[x] : 0.f;
+}
+
+__global__ void __launch_bounds__(kBlock) mm_set_kernel(StepArgs a, const float* __restrict__ in,
+                                                        float* __restrict__ rest1) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= a.g.n) return;
+    const int n = a.g.n;
+    float4* __restrict__ fout = static_cast<float4*>(a.fout);
+    const Neighbourhood h = neighbourhood(a.g, y);
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        const int x = shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h);
+        fout[(size_t)d * n + y] = make_float4(in[(size_t)(2 * d) * n + x], in[(size_t)(2 * d + 1) * n + x],
+                                              in[(size_t)(24 + 2 * d) * n + x], in[(size_t)(25 + 2 * d) * n + x]);
+    });
+    if (a.rho_out) a.rho_out[y] = in[(size_t)48 * n + y];
+    if (rest1) rest1[y] = in[(size_t)49 * n + y];
+}
+
+// Per-block partial sums of (1/2)(E.D + B.H), sum f^2 and rho_c over a grid-stride range of cells
+// (external current taken as zero here; the special-cell pass adds the correction).
+template <int M, bool kRho>
+__global__ void __launch_bounds__(kBlock) mm_reduce_kernel(StepArgs a, const float* __restrict__ rest1,
+                                                           double* __restrict__ partials) {
+    double w = 0.0, f2 = 0.0, q = 0.0;
+    const int n = a.g.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Neighbourhood h = neighbourhood(a.g, i);
+        float4 f[12];
+        mm_pull(static_cast<const float4*>(a.fin), n, h, f);
+        const float3 mat = load_material<M>(a.media, i);
+        float rest0 = 0.f;
+        if constexpr (kRho) rest0 = a.rho_in[i];
+        const MMFields F = mm_fields<kRho>(f, rest0, mat, make_float3(0.f, 0.f, 0.f));
+        const double inv2mu = 1.0 / (2.0 * (double)mat.y);
+        w += 0.5 * ((double)F.E.x * F.Dpp.x + (double)F.E.y * F.Dpp.y + (double)F.E.z * F.Dpp.z) +
+             0.5 * inv2mu * ((double)F.B.x * F.B.x + (double)F.B.y * F.B.y + (double)F.B.z * F.B.z);
+        double s = 0.0;
+#pragma unroll
+        for (int d = 0; d < 12; ++d)
+            s += (double)f[d].x * f[d].x + (double)f[d].y * f[d].y + (double)f[d].z * f[d].z +
+                 (double)f[d].w * f[d].w;
+        if constexpr (kRho) {
+            s += (double)rest0 * rest0;
+            q += F.rho;
+        }
+        if (rest1) s += (double)rest1[i] * rest1[i];
+        f2 += s;
+    }
+    block_sum3_store(w, f2, q, partials + 3 * blockIdx.x);
+}
+
+// Energy correction at source cells: (energy with J_ext) - (energy with J_ext = 0).
+template <int M>
+__global__ void __launch_bounds__(kBlock) mm_reduce_special_kernel(StepArgs a, double* __restrict__ partials) {
+    double w = 0.0;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < a.sv.n_special) {
+        const int i = a.sv.cell[m];
+        const Neighbourhood h = neighbourhood(a.g, i);
+        float4 f[12];
+        mm_pull(static_cast<const float4*>(a.fin), a.g.n, h, f);
+        const float3 mat = load_material<M>(a.media, i);
+        const MMFields F1 = mm_fields<false>(f, 0.f, mat, cell_source(a.sv, a.sc, m).J);
+        const MMFields F0 = mm_fields<false>(f, 0.f, mat, make_float3(0.f, 0.f, 0.f));
+        w = 0.5 * ((double)F1.E.x * F1.Dpp.x + (double)F1.E.y * F1.Dpp.y + (double)F1.E.z * F1.Dpp.z) -
+            0.5 * ((double)F0.E.x * F0.Dpp.x + (double)F0.E.y * F0.Dpp.y + (double)F0.E.z * F0.Dpp.z);
+    }
+    block_sum3_store(w, 0.0, 0.0, partials + 3 * blockIdx.x);
+}
+
+inline int blocks_for(int n) { return (n + kBlock - 1) / kBlock; }
+
+}  // namespace
+
+int mm_launch_step(const StepArgs& a, cudaStream_t st) {
+    const bool rho = a.rho_in != nullptr;
+    const int nb = blocks_for(a.g.n);
+#define MM_STEP(M, S, R, NB) mm_step_kernel<M, S, R><<<NB, kBlock, 0, st>>>(a)
+    int launched = 1;
+    switch (a.media_mode) {
+        case kUniform: rho ? MM_STEP(kUniform, false, true, nb) : MM_STEP(kUniform, false, false, nb); break;
+        case kTable: rho ? MM_STEP(kTable, false, true, nb) : MM_STEP(kTable, false, false, nb); break;
+        default: rho ? MM_STEP(kPerCell, false, true, nb) : MM_STEP(kPerCell, false, false, nb); break;
+    }
+    if (a.sv.n_special > 0) {
+        const int ns = blocks_for(a.sv.n_special);
+        switch (a.media_mode) {
+            case kUniform: rho ? MM_STEP(kUniform, true, true, ns) : MM_STEP(kUniform, true, false, ns); break;
+            case kTable: rho ? MM_STEP(kTable, true, true, ns) : MM_STEP(kTable, true, false, ns); break;
+            default: rho ? MM_STEP(kPerCell, true, true, ns) : MM_STEP(kPerCell, true, false, ns); break;
+        }
+        ++launched;
+    }
+#undef MM_STEP
+    return launched;
+}
+
+int mm_launch_init(const StepArgs& a, const float* E, const float* B, cudaStream_t st) {
+    const int nb = blocks_for(a.g.n);
+    switch (a.media_mode) {
+        case kUniform: mm_init_kernel<kUniform><<<nb, kBlock, 0, st>>>(a, E, B); break;
+        case kTable: mm_init_kernel<kTable><<<nb, kBlock, 0, st>>>(a, E, B); break;
+        default: mm_init_kernel<kPerCell><<<nb, kBlock, 0, st>>>(a, E, B); break;
+    }
+    return 1;
+}
+
+int mm_launch_fields(const StepArgs& a, FieldsOut out, cudaStream_t st) {
+    const int nb = blocks_for(a.g.n);
+    int launched = 1;
+    switch (a.media_mode) {
+        case kUniform: mm_fields_kernel<kUniform, false, false><<<nb, kBlock, 0, st>>>(a, out); break;
+        case kTable: mm_fields_kernel<kTable, false, false><<<nb, kBlock, 0, st>>>(a, out); break;
+        default: mm_fields_kernel<kPerCell, false, false><<<nb, kBlock, 0, st>>>(a, out); break;
+    }
+    if (a.sv.n_special > 0) {
+        const int ns = blocks_for(a.sv.n_special);
+        switch (a.media_mode) {
+            case kUniform: mm_fields_kernel<kUniform, true, false><<<ns, kBlock, 0, st>>>(a, out); break;
+            case kTable: mm_fields_kernel<kTable, true, false><<<ns, kBlock, 0, st>>>(a, out); break;
+            default: mm_fields_kernel<kPerCell, true, false><<<ns, kBlock, 0, st>>>(a, out); break;
+        }
+        ++launched;
+    }
+    return launched;
+}
+
+int mm_launch_get(const StepArgs& a, float* out, cudaStream_t st) {
+    mm_get_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, static_cast<const float*>(a.fin2), out);
+    return 1;
+}
+
+int mm_launch_set(const StepArgs& a, const float* in, cudaStream_t st) {
+    mm_set_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, in, static_cast<float*>(a.fout2));
+    return 1;
+}
+
+int mm_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* result, cudaStream_t st) {
+    const bool rho = a.rho_in != nullptr;
+    const float* rest1 = static_cast<const float*>(a.fin2);
+    switch (a.media_mode) {
+        case kUniform:
+            rho ? mm_reduce_kernel<kUniform, true><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials)
+                : mm_reduce_kernel<kUniform, false><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
+            break;
+        case kTable:
+            rho ? mm_reduce_kernel<kTable, true><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials)
+                : mm_reduce_kernel<kTable, false><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
+            break;
+        default:
+            rho ? mm_reduce_kernel<kPerCell, true><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials)
+                : mm_reduce_kernel<kPerCell, false><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
+            break;
+    }
+    int total = n_blocks, launched = 1;
+    if (a.sv.n_special > 0) {
+        const int ns = blocks_for(a.sv.n_special);
+        double* p2 = partials + 3 * n_blocks;
+        switch (a.media_mode) {
+            case kUniform: mm_reduce_special_kernel<kUniform><<<ns, kBlock, 0, st>>>(a, p2); break;
+            case kTable: mm_reduce_special_kernel<kTable><<<ns, kBlock, 0, st>>>(a, p2); break;
+            default: mm_reduce_special_kernel<kPerCell><<<ns, kBlock, 0, st>>>(a, p2); break;
+        }
+        total += ns;
+        ++launched;
+    }
+    return launched + launch_reduce_partials(partials, total, result, st);
+}
+
+}  // namespace lbm
