@@ -36,14 +36,14 @@ FALLBACK_HBM_GBS = 6800.0
 PROFILE_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(files) -> str:
+    """Hash of the source files that define a kernel (so a stale ncu record is detected)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2309_08068_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode())
-                h.update(fh.read())
+    for name in sorted(files):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -65,7 +65,7 @@ def ncu_traffic(kernel: str, n_cells: int):
     except Exception:
         return None
     entry = prof.get(kernel)
-    if not entry or entry.get("source_hash") != kernel_source_hash():
+    if not entry or entry.get("source_hash") != kernel_source_hash(entry["sources"]):
         return None
     return entry["dram_bytes_per_launch"] * n_cells / entry["cells"]
 
@@ -301,6 +301,7 @@ def run_ours(args):
     mm_gbs = BYTES_PER_CELL["mm"] * ncell / (mm_ms * 1e-3) / 1e9
     hv_gbs = BYTES_PER_CELL["hv"] * ncell / (hv_ms * 1e-3) / 1e9
     traffic = ncu_traffic("mm_step_kernel", ncell)
+    hv_traffic = ncu_traffic("hv_step_kernel", ncell)
     cores = cpu_cores()
     cpu_mlups, cpu_steps, cpu_s = oracle_mlups(64, args.cpu_seconds, cores)
     line = {
@@ -317,7 +318,8 @@ def run_ours(args):
                    "algorithmic_GBps": round(mm_gbs, 1), "bytes_per_cell": BYTES_PER_CELL["mm"]},
             "hv": {"MLUPS": round(ncell / (hv_ms * 1e-3) / 1e6, 2), "ms_per_step": round(hv_ms, 4),
                    "algorithmic_GBps": round(hv_gbs, 1), "bytes_per_cell": BYTES_PER_CELL["hv"],
-                   "frac": round(hv_gbs / peak, 4)},
+                   "frac": round(hv_gbs / peak, 4),
+                   "traffic": None if hv_traffic is None else round(hv_traffic)},
         },
         "roofline": {"bound": "hbm", "kernel": "mm_step_kernel (+ source-cell launch)",
                      "achieved": round(mm_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
