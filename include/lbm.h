@@ -163,6 +163,23 @@ int lbm_reduce(lbm_ctx* ctx, double out[3]);
 /* LBM_OK if every stored population is finite, LBM_ENONFINITE otherwise. Waits for the stream. */
 int lbm_check_finite(lbm_ctx* ctx);
 
+/* lbm_reduce_noalloc: the same three values as lbm_reduce, computed without allocating any device
+ * memory. The paper has no counterpart; this entry point exists for callers that cannot allocate:
+ * those whose device memory belongs to a pool of their own, and those whose loop cannot take the
+ * implicit synchronisation of cudaMalloc/cudaFree. lbm_reduce may allocate its partial-sum buffer
+ * on first use; this call keeps the partial sums in a static device array that every GPU loading the
+ * library holds until exit (4096 slots of 3 doubles, 96 KiB). It calls no cudaMalloc or cudaFree.
+ *   out: 3 doubles. on_device = 1: device memory, written in stream order (no wait).
+ *        on_device = 0: host memory; the call waits for the stream.
+ * Limit: the lattice's reduction blocks (at most 608) plus one block per 256 source cells must fit
+ *   in the 4096 slots; otherwise LBM_EINVAL with a message giving the limit.
+ * The first call on a device looks up the static array's device address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture. Every call, from any context, shares the one
+ *   array: nothing in it needs to start at zero, but calls whose kernels overlap on the GPU (for
+ *   instance two contexts on different streams) race on it, so order them on one stream or wait in
+ *   between. */
+int lbm_reduce_noalloc(lbm_ctx* ctx, double* out, int on_device);
+
 /* Number of completed steps. */
 int64_t lbm_time(const lbm_ctx* ctx);
 /* Kernel launches enqueued by this context so far (all kinds). */

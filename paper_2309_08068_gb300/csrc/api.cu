@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -703,3 +704,74 @@ int launch_reduce_partials(const double* partials, int n_blocks, double* result,
     return 1;
 }
 }  // namespace lbm
+
+// ------------------------------------------------------------------------------------------------
+// lbm_reduce_noalloc: the reductions of lbm_reduce without any device allocation.
+//
+// lbm_reduce keeps its per-block partial sums in device memory that it allocates on first use (and
+// again when the source-cell list grows). Some callers cannot allow that: their device memory is
+// owned by a pool of their own that must account for every byte, or their stepping loop cannot take
+// the implicit device synchronisation of cudaMalloc/cudaFree. This entry point runs the same kernels
+// with the partial sums in the file-scope array below instead. Every GPU that loads the library
+// holds the array (about 96 KiB) until the process exits.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticPartialBlocks = 4096;  // partial-sum slots (3 doubles each); the size limit
+
+static __device__ __align__(256) double g_reduce_scratch[3 * kStaticPartialBlocks + 3];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_reduce_scratch on the current device, looked up once per device. In host
+// code the array's name is only a host-side stand-in, never a device address.
+int static_scratch(lbm_ctx* ctx, double** out) {
+    if (ctx->device < 0 || ctx->device >= kMaxDevices)
+        return fail(ctx, LBM_EUNSUPPORTED, "lbm_reduce_noalloc: device %d beyond the %d supported", ctx->device,
+                    kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_reduce_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, LBM_ECUDA, "lbm_reduce_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_scratch_addr[ctx->device] = static_cast<double*>(p);
+    }
+    *out = g_scratch_addr[ctx->device];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_reduce_noalloc(lbm_ctx* ctx, double* out, int on_device) {
+    if (!ctx) return LBM_EINVAL;
+    if (!out) return fail(ctx, LBM_EINVAL, "lbm_reduce_noalloc: out is NULL");
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    const int ns_blocks = ctx->n_special > 0 ? (ctx->n_special + kBlock - 1) / kBlock : 0;
+    const int needed = ctx->reduce_blocks + ns_blocks;
+    if (needed > kStaticPartialBlocks)
+        return fail(ctx, LBM_EINVAL,
+                    "lbm_reduce_noalloc: needs %d partial-sum slots but the static scratch holds %d "
+                    "(%d source cells is more than the %d it allows for this lattice)",
+                    needed, kStaticPartialBlocks, ctx->n_special, (kStaticPartialBlocks - ctx->reduce_blocks) * kBlock);
+    double* scratch = nullptr;
+    if ((rc = static_scratch(ctx, &scratch)) != LBM_OK) return rc;
+    // Every slot the final sum reads is written by this call's kernels first, so nothing needs
+    // clearing; the result lands in the caller's device buffer or in the last 3 slots.
+    double* result = on_device ? out : scratch + 3 * kStaticPartialBlocks;
+    StepArgs a = base_args(ctx);
+    bind_buffers(ctx, a, ctx->cur, 1 - ctx->cur);
+    fill_scalars(ctx, a, ctx->t + 1);
+    const int launched = ctx->model == LBM_MM
+                             ? mm_launch_reduce(a, scratch, ctx->reduce_blocks, result, ctx->stream)
+                             : hv_launch_reduce(a, scratch, ctx->reduce_blocks, result, ctx->stream);
+    if ((rc = check_launch(ctx, launched)) != LBM_OK) return rc;
+    if (!on_device) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(out, result, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return LBM_OK;
+}
