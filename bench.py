@@ -32,6 +32,8 @@ from paper_2309_08068_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "MLUPS"
 BYTES_PER_CELL = {"mm": 384, "hv": 288}  # FP32 populations read + written; vacuum needs no media bytes
+POPULATION_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
+F16_SCALE = 2.0 ** 20  # keeps populations of 1e-4-amplitude fields in FP16's normal range
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -182,6 +184,30 @@ def oracle_mlups(n_side: int, budget_s: float, threads: int, steps: int | None =
     return total_updates / total_s / 1e6, done, total_s
 
 
+def storage_accuracy(storages=("f32", "bf16", "f16")):
+    """Relative L2 error of E and B against the FP64 oracle after the 1500-step dielectric pulse
+    (1 x 1 x 1024, eps_r = 2.5 slab) for each storage, both models."""
+    from oracle import OracleLattice
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    out = {st: {} for st in storages}
+    for model in ("mm", "hv"):
+        w = wl.dielectric_pulse_1d(model)
+        w.eps_r = np.asarray(w.eps_r, np.float32).astype(np.float64)
+        w.E = np.asarray(w.E, np.float32).astype(np.float64)
+        w.B = np.asarray(w.B, np.float32).astype(np.float64)
+        O = OracleLattice(model, w.shape, w.eps_r)
+        O.init_fields(w.E, w.B)
+        O.step(w.steps)
+        o = O.fields()
+        for st in storages:
+            L = lattice_from_workload(w, storage=st, storage_scale=F16_SCALE if st == "f16" else 0.0)
+            L.step(w.steps)
+            g = L.fields_host("EB")
+            out[st][model] = {c: float(np.linalg.norm(g[c] - o[c]) / np.linalg.norm(o[c])) for c in "EB"}
+            L.close()
+    return out
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -233,10 +259,11 @@ def run_ours(args):
     ncell = n_side ** 3
     stream = torch.cuda.Stream()
     lats = {}
+    scale = F16_SCALE if args.storage == "f16" else 0.0
     with torch.cuda.stream(stream):
         for model in ("mm", "hv"):
             w = wl.hertz_dipole(model, n=n_side, period=32.0)
-            lats[model] = lattice_from_workload(w, stream=stream)
+            lats[model] = lattice_from_workload(w, stream=stream, storage=args.storage, storage_scale=scale)
     torch.cuda.synchronize()
 
     def one_step(ev=None):
@@ -271,6 +298,34 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     finite = all(L.check_finite() for L in lats.values())
 
+    # 16-bit storage variants on the same workload (shorter timed run each)
+    variants = {}
+    for st in ("bf16", "f16"):
+        variants[st] = {}
+        for model in ("mm", "hv"):
+            with torch.cuda.stream(stream):
+                w = wl.hertz_dipole(model, n=n_side, period=32.0)
+                Lv = lattice_from_workload(w, stream=stream, storage=st,
+                                           storage_scale=F16_SCALE if st == "f16" else 0.0)
+            for _ in range(args.warmup):
+                Lv.step(1)
+            kv = max(10, min(args.steps, 200))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(kv):
+                Lv.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / kv
+            nbytes = BYTES_PER_CELL[model] // 2
+            variants[st][model] = {"MLUPS": round(ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
+                                   "bytes_per_cell": nbytes,
+                                   "algorithmic_GBps": round(nbytes * ncell / (ms * 1e-3) / 1e9, 1),
+                                   "steps_timed": kv}
+            Lv.close()
+    accuracy = storage_accuracy() if rank == 0 else None
+
     # end to end through the C ABI with host buffers: upload fields, K steps, read E and B back
     pinned_E = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
     pinned_B = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
@@ -298,16 +353,19 @@ def run_ours(args):
 
     value = job_value(2 * ncell, args.steps, world, elapsed_ms * 1e-3)
     peak, peak_kind = hbm_peak()
-    mm_gbs = BYTES_PER_CELL["mm"] * ncell / (mm_ms * 1e-3) / 1e9
-    hv_gbs = BYTES_PER_CELL["hv"] * ncell / (hv_ms * 1e-3) / 1e9
-    traffic = ncu_traffic("mm_step_kernel", ncell)
-    hv_traffic = ncu_traffic("hv_step_kernel", ncell)
+    shrink = 4 // POPULATION_BYTES[args.storage]
+    bpc = {m: BYTES_PER_CELL[m] // shrink for m in BYTES_PER_CELL}
+    mm_gbs = bpc["mm"] * ncell / (mm_ms * 1e-3) / 1e9
+    hv_gbs = bpc["hv"] * ncell / (hv_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("mm_step_kernel", ncell) if args.storage == "f32" else None
+    hv_traffic = ncu_traffic("hv_step_kernel", ncell) if args.storage == "f32" else None
     cores = cpu_cores()
     cpu_mlups, cpu_steps, cpu_s = oracle_mlups(64, args.cpu_seconds, cores)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "storage": args.storage,
         "data": "synthetic",
         "config": {"workload": f"hertz_dipole_{n_side}^3_mm+hv", "cells_per_model": ncell,
                    "step": "one MM step + one HV step, each on its own lattice", "period": 32, "J0": 1e-4,
@@ -315,9 +373,9 @@ def run_ours(args):
                    "parallelism": f"independent lattices per rank x{world}"},
         "per_model": {
             "mm": {"MLUPS": round(ncell / (mm_ms * 1e-3) / 1e6, 2), "ms_per_step": round(mm_ms, 4),
-                   "algorithmic_GBps": round(mm_gbs, 1), "bytes_per_cell": BYTES_PER_CELL["mm"]},
+                   "algorithmic_GBps": round(mm_gbs, 1), "bytes_per_cell": bpc["mm"]},
             "hv": {"MLUPS": round(ncell / (hv_ms * 1e-3) / 1e6, 2), "ms_per_step": round(hv_ms, 4),
-                   "algorithmic_GBps": round(hv_gbs, 1), "bytes_per_cell": BYTES_PER_CELL["hv"],
+                   "algorithmic_GBps": round(hv_gbs, 1), "bytes_per_cell": bpc["hv"],
                    "frac": round(hv_gbs / peak, 4),
                    "traffic": None if hv_traffic is None else round(hv_traffic)},
         },
@@ -330,6 +388,10 @@ def run_ours(args):
         "e2e": {"value": round(job_value(2 * ncell, e2e_steps, world, e2e_s), 2), "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
                 "job": f"lbm_init_fields from pinned host E, B + {e2e_steps} steps + lbm_fields E, B to host"},
+        "storage_variants": {
+            st: {m: dict(v, frac=round(v["algorithmic_GBps"] / peak, 4)) for m, v in variants[st].items()}
+            for st in variants},
+        "rel_l2_vs_fp64_dielectric_pulse_1500": accuracy,
         "gpu_launches": int(launches),
         "finite": finite,
         "clocks": clocks.summary(),
@@ -348,6 +410,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
+                    help="population storage of the main timed run (arithmetic is FP32 in every case)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -41,7 +41,9 @@ enum {
     LBM_EUNSUPPORTED = -6  /* valid request this build does not implement */
 };
 
-/* Population storage precision. Only LBM_F32 is implemented; arithmetic is always FP32. */
+/* Population storage precision; arithmetic is FP32 in every case. LBM_BF16 and LBM_F16 store each
+ * population in 16 bits (half the bytes of a bandwidth-bound step) as f * storage_scale, rounded to
+ * nearest; the survey of 16-bit storage error is in the design notes. */
 enum { LBM_F32 = 0, LBM_BF16 = 1, LBM_F16 = 2 };
 
 /* Per-cell linear media (Section I-B remark: eps = eps_r eps0, mu = mu_r mu0). Each pointer is an
@@ -57,7 +59,11 @@ typedef struct {
 } lbm_media;
 
 /* Context options; pass NULL for all defaults.
- * storage: LBM_F32.  cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ * storage: LBM_F32, LBM_BF16 or LBM_F16.  cuda_stream: a cudaStream_t, or NULL for the legacy
+ *   default stream.
+ * storage_scale: 16-bit storage keeps f * storage_scale; a power of two (so scaling is exact), 0 for
+ *   1. FP16 needs it to keep small populations out of subnormals (FP16's smallest normal is 6.1e-5)
+ *   and large ones below 65504; BF16 has FP32's range. Ignored for LBM_F32.
  * track_rho: MM only; also store the rest populations f_0^(0), f_0^(1), so that rho_c (eq.
  *   MacroscopicFieldsMiller) is kept and lbm_get_populations returns them. Otherwise the rest
  *   populations are not stored (neither enters E, B, D, H or J) and read back as 0.
@@ -70,6 +76,7 @@ typedef struct {
     int track_rho;
     double eps0;
     double mu0;
+    double storage_scale;
 } lbm_options;
 
 /* Time dependence s(t) of a source, evaluated on the host in double precision for iteration t.

@@ -41,6 +41,8 @@ struct lbm_ctx {
     int track_rho = 0;
     double eps0 = 0, mu0 = 0;
     int device = 0;
+    int storage = LBM_F32;
+    float scale = 1.f;
     // populations (pull scheme, two buffers)
     void* buf[2] = {nullptr, nullptr};   // MM float4[12][n]; HV float4[6][n]
     void* buf2[2] = {nullptr, nullptr};  // HV float2[6][n]
@@ -49,9 +51,9 @@ struct lbm_ctx {
     int cur = 0;
     // media
     int media_mode = kUniform;
-    float4 uniform = make_float4(1.f, 1.f, 0.f, 0.f);
+    MatCoef uniform{};
     uint8_t* mat_id = nullptr;
-    float4* mat_table = nullptr;
+    MatCoef* mat_table = nullptr;
     float* eps_r = nullptr;
     float* mu_r = nullptr;
     float* sigma = nullptr;
@@ -107,7 +109,13 @@ int ensure_device(lbm_ctx* ctx) {
     return LBM_OK;
 }
 
-size_t group_bytes(int model) { return model == LBM_MM ? 12 * sizeof(float4) : 6 * sizeof(float4); }
+// Bytes per cell of the main population array (MM: 12 groups of 4; HV: 6 groups of 4) and of HV's
+// second array (6 groups of 2).
+size_t group_bytes(int model, int storage) {
+    const size_t v4 = storage == LBM_F32 ? sizeof(float4) : 4 * sizeof(uint16_t);
+    return model == LBM_MM ? 12 * v4 : 6 * v4;
+}
+size_t pair_bytes(int storage) { return 6 * (storage == LBM_F32 ? sizeof(float2) : 2 * sizeof(uint16_t)); }
 
 StepArgs base_args(lbm_ctx* c) {
     StepArgs a;
@@ -134,6 +142,9 @@ StepArgs base_args(lbm_ctx* c) {
     }
     a.eps0 = (float)c->eps0;
     a.mu0 = (float)c->mu0;
+    a.storage = c->storage;
+    a.scale = c->scale;
+    a.inv_scale = 1.f / c->scale;
     return a;
 }
 
@@ -251,11 +262,36 @@ int fetch_host(lbm_ctx* c, const float* p, int on_device, int64_t n, std::vector
     return LBM_OK;
 }
 
+// Coefficients of one material (see MatCoef). Reciprocals used by div_rn are RN(1/d) of the
+// stored float d, computed as a float division.
+MatCoef coef_for(const lbm_ctx* c, float er, float mr, float sg) {
+    MatCoef k;
+    if (c->model == LBM_MM) {
+        const double g = 1.0 / (1.0 + c->mu0 * (double)sg / (4.0 * (double)er));
+        k.c0 = make_float4(er, 1.0f / er, (float)g, (float)(0.25 / (double)mr));
+        k.c1 = make_float4(sg, mr, 0.f, 0.f);
+    } else {
+        const float eps = (float)(c->eps0 * (double)er), mu = (float)(c->mu0 * (double)mr);
+        k.c0 = make_float4(eps, 1.0f / eps, mu, 1.0f / mu);
+        k.c1 = make_float4(sg, er, 0.f, 0.f);
+    }
+    return k;
+}
+
+// Magic multiplier for division by d of indices below 2^31: k = ceil(log2 d), M = ceil(2^(32+k) / d).
+void magic_for(int d, unsigned long long* M, int* k) {
+    int kk = 0;
+    while ((1LL << kk) < (long long)d) ++kk;
+    const unsigned __int128 num = (unsigned __int128)1 << (32 + kk);
+    *M = (unsigned long long)((num + (unsigned)d - 1) / (unsigned)d);
+    *k = kk;
+}
+
 int setup_media(lbm_ctx* c, const lbm_media* m) {
     const int64_t n = c->g.n;
     if (!m || (!m->eps_r && !m->mu_r && !m->sigma)) {
         c->media_mode = kUniform;
-        c->uniform = make_float4(1.f, 1.f, 0.f, 0.f);
+        c->uniform = coef_for(c, 1.f, 1.f, 0.f);
         return LBM_OK;
     }
     std::vector<float> er, mr, sg;
@@ -287,21 +323,20 @@ int setup_media(lbm_ctx* c, const lbm_media* m) {
     if (table_ok && ids.size() == 1) {
         auto key = ids.begin()->first;
         c->media_mode = kUniform;
-        c->uniform = make_float4(std::get<0>(key), std::get<1>(key), std::get<2>(key), 0.f);
+        c->uniform = coef_for(c, std::get<0>(key), std::get<1>(key), std::get<2>(key));
         return LBM_OK;
     }
     if (table_ok) {
-        std::vector<float4> table(ids.size());
+        std::vector<MatCoef> table(ids.size());
         for (auto& kv : ids)
-            table[(size_t)kv.second] =
-                make_float4(std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), 0.f);
+            table[(size_t)kv.second] = coef_for(c, std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first));
         if (cudaMalloc(&c->mat_id, (size_t)n) != cudaSuccess ||
-            cudaMalloc(&c->mat_table, sizeof(float4) * table.size()) != cudaSuccess) {
+            cudaMalloc(&c->mat_table, sizeof(MatCoef) * table.size()) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, LBM_ENOMEM, "cannot allocate the material table");
         }
         CUDA_TRY(c, cudaMemcpy(c->mat_id, id.data(), (size_t)n, cudaMemcpyHostToDevice));
-        CUDA_TRY(c, cudaMemcpy(c->mat_table, table.data(), sizeof(float4) * table.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->mat_table, table.data(), sizeof(MatCoef) * table.size(), cudaMemcpyHostToDevice));
         c->media_mode = kTable;
         return LBM_OK;
     }
@@ -366,8 +401,15 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: dimensions must be >= 1");
     const int64_t n = (int64_t)nx * ny * nz;
     if (n > (int64_t)INT32_MAX) return fail(nullptr, LBM_EINVAL, "lbm_create: %lld cells exceed 2^31 - 1", (long long)n);
-    if (opts && opts->storage != LBM_F32)
-        return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only LBM_F32 population storage is built");
+    const int storage = opts ? opts->storage : LBM_F32;
+    if (storage != LBM_F32 && storage != LBM_BF16 && storage != LBM_F16)
+        return fail(nullptr, LBM_EINVAL, "lbm_create: unknown storage %d", storage);
+    double scale = (opts && storage != LBM_F32) ? opts->storage_scale : 0.0;
+    if (scale == 0.0) scale = 1.0;
+    int scale_exp = 0;
+    if (!(scale > 0) || !std::isfinite(scale) || std::frexp(scale, &scale_exp) != 0.5 || scale_exp < -100 ||
+        scale_exp > 100)
+        return fail(nullptr, LBM_EINVAL, "lbm_create: storage_scale must be a power of two in [2^-100, 2^100]");
     double eps0 = opts ? opts->eps0 : 0.0, mu0 = opts ? opts->mu0 : 0.0;
     if (eps0 < 0 || mu0 < 0 || !std::isfinite(eps0) || !std::isfinite(mu0))
         return fail(nullptr, LBM_EINVAL, "lbm_create: eps0, mu0 must be >= 0");
@@ -383,21 +425,26 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(nullptr, LBM_ENOMEM, "lbm_create: out of host memory");
     c->model = model;
-    c->g = Geometry{nx, ny, nz, (int)n};
+    c->g = Geometry{nx, ny, nz, (int)n, 0, 0, 0, 0};
+    magic_for(nx, &c->g.mx, &c->g.kx);
+    magic_for(nx * ny, &c->g.mxy, &c->g.kxy);
     c->stream = opts ? static_cast<cudaStream_t>(opts->cuda_stream) : nullptr;
     c->track_rho = (opts && opts->track_rho && model == LBM_MM) ? 1 : 0;
     c->eps0 = eps0;
     c->mu0 = mu0;
+    c->storage = storage;
+    c->scale = (float)scale;
     int rc;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return fail(nullptr, LBM_ECUDA, "lbm_create: no CUDA device");
     }
-    const size_t pop_bytes = group_bytes(model) * (size_t)n;
+    const size_t pop_bytes = group_bytes(model, storage) * (size_t)n;
+    const size_t pop2_bytes = pair_bytes(storage) * (size_t)n;
     for (int b = 0; b < 2; ++b) {
         bool ok = cudaMalloc(&c->buf[b], pop_bytes) == cudaSuccess;
-        if (ok && model == LBM_HV) ok = cudaMalloc(&c->buf2[b], 6 * sizeof(float2) * (size_t)n) == cudaSuccess;
+        if (ok && model == LBM_HV) ok = cudaMalloc(&c->buf2[b], pop2_bytes) == cudaSuccess;
         if (ok && c->track_rho) ok = cudaMalloc(&c->rho[b], sizeof(float) * (size_t)n) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
@@ -428,7 +475,7 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
     bool zero_ok = true;
     for (int b = 0; b < 2; ++b) {
         zero_ok &= cudaMemsetAsync(c->buf[b], 0, pop_bytes, c->stream) == cudaSuccess;
-        if (c->buf2[b]) zero_ok &= cudaMemsetAsync(c->buf2[b], 0, 6 * sizeof(float2) * (size_t)n, c->stream) == cudaSuccess;
+        if (c->buf2[b]) zero_ok &= cudaMemsetAsync(c->buf2[b], 0, pop2_bytes, c->stream) == cudaSuccess;
         if (c->rho[b]) zero_ok &= cudaMemsetAsync(c->rho[b], 0, sizeof(float) * (size_t)n, c->stream) == cudaSuccess;
     }
     if (c->rest1) zero_ok &= cudaMemsetAsync(c->rest1, 0, sizeof(float) * (size_t)n, c->stream) == cudaSuccess;

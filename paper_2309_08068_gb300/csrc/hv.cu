@@ -1,7 +1,8 @@
 // Modified Hauser-Verhey (HV) model kernels, arXiv 2309.08068 Section III.
 //
 // One thread updates one cell: 6 directions, each an electric vector e_i and a magnetic vector h_i
-// (36 scalars), pulled as a float4 (e_x, e_y, e_z, h_x) and a float2 (h_y, h_z) from cell x - v_i.
+// (36 scalars), pulled as a 4-vector (e_x, e_y, e_z, h_x) and a 2-vector (h_y, h_z) from cell
+// x - v_i (float4 + float2, or 8 + 4 bytes with 16-bit storage); arithmetic is FP32.
 // Velocities in the Section III order: v1 = +x, v2 = +y, v3 = -x, v4 = -y, v5 = -z, v6 = +z.
 //
 // With tau = 1/2 the collision (eqs. equilibriumHV, CollisionHV, CollisionmodifiedHV) is
@@ -44,22 +45,32 @@ __device__ __forceinline__ int push_index(const Neighbourhood& h) {
     return shifted<a == 0 ? s : 0, a == 1 ? s : 0, a == 2 ? s : 0>(h);
 }
 
-__device__ __forceinline__ void hv_pull(const float4* __restrict__ ein, const float2* __restrict__ hin, int n,
-                                        const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) {
+template <int S>
+__device__ __forceinline__ void hv_pull(const StepArgs& a, const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) {
+    const auto* __restrict__ ein = static_cast<const typename Pack4<S>::T*>(a.fin);
+    const auto* __restrict__ hin = static_cast<const typename Pack2<S>::T*>(a.fin2);
     static_for<0, 6>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         const int src = pull_index<i>(h);
-        e[i] = __ldg(ein + (size_t)i * n + src);
-        hy[i] = __ldg(hin + (size_t)i * n + src);
+        e[i] = Pack4<S>::load(ein + (size_t)i * a.g.n + src, a.inv_scale);
+        hy[i] = Pack2<S>::load(hin + (size_t)i * a.g.n + src, a.inv_scale);
     });
+}
+
+template <int S>
+__device__ __forceinline__ void hv_put(const StepArgs& a, int k, int i, float4 e, float2 hy) {
+    auto* __restrict__ eout = static_cast<typename Pack4<S>::T*>(a.fout);
+    auto* __restrict__ hout = static_cast<typename Pack2<S>::T*>(a.fout2);
+    eout[(size_t)k * a.g.n + i] = Pack4<S>::pack(e, a.scale);
+    hout[(size_t)k * a.g.n + i] = Pack2<S>::pack(hy, a.scale);
 }
 
 struct HVFields {
     float3 D, B, E, H, J;
 };
 
-__device__ __forceinline__ HVFields hv_fields(const float4 (&e)[6], const float2 (&hy)[6], float3 mat, float eps0,
-                                              float mu0, float3 jext) {
+__device__ __forceinline__ HVFields hv_fields(const float4 (&e)[6], const float2 (&hy)[6], const MatCoef& mat,
+                                              float3 jext) {
     HVFields F;
     // Pairwise sums ((1 + 2) + (3 + 4)) + (5 + 6) over the directions.
     float tx[6], ty[6], tz[6], ux[6], uy[6], uz[6];
@@ -78,16 +89,33 @@ __device__ __forceinline__ HVFields hv_fields(const float4 (&e)[6], const float2
     const float bx = pairwise_sum<0, 4>(ux) + pairwise_sum<4, 6>(ux);
     const float by = pairwise_sum<0, 4>(uy) + pairwise_sum<4, 6>(uy);
     const float bz = pairwise_sum<0, 4>(uz) + pairwise_sum<4, 6>(uz);
-    const float eps = eps0 * mat.x, mu = mu0 * mat.y;
+    const float eps = mat.c0.x, inv_eps = mat.c0.y, mu = mat.c0.z, inv_mu = mat.c0.w, sigma = mat.c1.x;
     F.D = make_float3(dx, dy, dz);
     F.B = make_float3(bx, by, bz);
-    F.E = make_float3(dx / eps, dy / eps, dz / eps);
-    F.H = make_float3(bx / mu, by / mu, bz / mu);
-    F.J = make_float3(mat.z * F.E.x + jext.x, mat.z * F.E.y + jext.y, mat.z * F.E.z + jext.z);
+    F.E = make_float3(div_rn(dx, eps, inv_eps), div_rn(dy, eps, inv_eps), div_rn(dz, eps, inv_eps));
+    F.H = make_float3(div_rn(bx, mu, inv_mu), div_rn(by, mu, inv_mu), div_rn(bz, mu, inv_mu));
+    F.J = make_float3(sigma * F.E.x + jext.x, sigma * F.E.y + jext.y, sigma * F.E.z + jext.z);
     return F;
 }
 
-template <int M, bool kSpecial>
+constexpr float kInv3 = 1.0f / 3.0f;  // RN(1/3)
+constexpr float kInv6 = 1.0f / 6.0f;  // RN(1/6)
+
+__device__ __forceinline__ float3 sixth(float3 v) {
+    return make_float3(div_rn(v.x, 6.f, kInv6), div_rn(v.y, 6.f, kInv6), div_rn(v.z, 6.f, kInv6));
+}
+// D / 6 with D = eps E.
+__device__ __forceinline__ float3 hv_sixth_of_d(float3 E, const MatCoef& mat) {
+    const float eps = mat.c0.x;
+    return sixth(make_float3(eps * E.x, eps * E.y, eps * E.z));
+}
+// H = B / mu.
+__device__ __forceinline__ float3 hv_h(float3 B, const MatCoef& mat) {
+    const float mu = mat.c0.z, inv_mu = mat.c0.w;
+    return make_float3(div_rn(B.x, mu, inv_mu), div_rn(B.y, mu, inv_mu), div_rn(B.z, mu, inv_mu));
+}
+
+template <int S, int M, bool kSpecial>
 __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
     int i, m = 0;
     if constexpr (kSpecial) {
@@ -98,28 +126,27 @@ __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
         i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= a.g.n) return;
     }
-    const int n = a.g.n;
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 e[6];
     float2 hy[6];
-    hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
-    const float3 mat = load_material<M>(a.media, i);
+    hv_pull<S>(a, h, e, hy);
+    const MatCoef mat = load_coef<kModelHV, M>(a.media, i, a.eps0, a.mu0);
     CellSource cs;
     float3 jext = make_float3(0.f, 0.f, 0.f);
     if constexpr (kSpecial) {
         cs = cell_source(a.sv, a.sc, m);
         jext = cs.J;
     }
-    const HVFields F = hv_fields(e, hy, mat, a.eps0, a.mu0, jext);
-    const float3 q = make_float3(F.D.x / 3.f, F.D.y / 3.f, F.D.z / 3.f);
-    const float3 p = make_float3(F.B.x / 3.f, F.B.y / 3.f, F.B.z / 3.f);
-    float4* __restrict__ eout = static_cast<float4*>(a.fout);
-    float2* __restrict__ hout = static_cast<float2*>(a.fout2);
+    const HVFields F = hv_fields(e, hy, mat, jext);
+    // Isotropic share of 2 e^eq and 2 h^eq: D / 3 and B / 3, correctly rounded (a multiplication by
+    // RN(1/3) would bias every step by the same relative 3e-8 and drift D and B on long runs).
+    const float3 q = make_float3(div_rn(F.D.x, 3.f, kInv3), div_rn(F.D.y, 3.f, kInv3), div_rn(F.D.z, 3.f, kInv3));
+    const float3 p = make_float3(div_rn(F.B.x, 3.f, kInv3), div_rn(F.B.y, 3.f, kInv3), div_rn(F.B.z, 3.f, kInv3));
     static_for<0, 6>([&](auto ic) {
         constexpr int k = decltype(ic)::value;
-        constexpr int A = kHVAxis[k], S = kHVSign[k];
-        const float3 vH = axis_cross<A, S>(F.H);
-        const float3 vE = axis_cross<A, S>(F.E);
+        constexpr int A = kHVAxis[k], G = kHVSign[k];
+        const float3 vH = axis_cross<A, G>(F.H);
+        const float3 vE = axis_cross<A, G>(F.E);
         float3 eo = make_float3(q.x - vH.x - e[k].x, q.y - vH.y - e[k].y, q.z - vH.z - e[k].z);
         // eq. SourceTermHV: T_i = -(J . v_i) v_i / 2 = -(J_A / 2) along axis A.
         if constexpr (A == 0) eo.x -= 0.5f * F.J.x;
@@ -128,50 +155,44 @@ __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
         float3 ho = make_float3(p.x + vE.x - e[k].w, p.y + vE.y - hy[k].x, p.z + vE.z - hy[k].y);
         if constexpr (kSpecial) {
             if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
-                const float eps = a.eps0 * mat.x, mu = a.mu0 * mat.y;
-                const float3 Hi = make_float3(cs.B.x / mu, cs.B.y / mu, cs.B.z / mu);
-                const float3 cH = axis_cross<A, S>(Hi);
-                const float3 cE = axis_cross<A, S>(cs.E);
-                eo = make_float3((eps * cs.E.x) / 6.f - 0.5f * cH.x, (eps * cs.E.y) / 6.f - 0.5f * cH.y,
-                                 (eps * cs.E.z) / 6.f - 0.5f * cH.z);
-                ho = make_float3(cs.B.x / 6.f + 0.5f * cE.x, cs.B.y / 6.f + 0.5f * cE.y, cs.B.z / 6.f + 0.5f * cE.z);
+                const float3 cH = axis_cross<A, G>(hv_h(cs.B, mat));
+                const float3 cE = axis_cross<A, G>(cs.E);
+                const float3 d6 = hv_sixth_of_d(cs.E, mat), b6 = sixth(cs.B);
+                eo = make_float3(d6.x - 0.5f * cH.x, d6.y - 0.5f * cH.y, d6.z - 0.5f * cH.z);
+                ho = make_float3(b6.x + 0.5f * cE.x, b6.y + 0.5f * cE.y, b6.z + 0.5f * cE.z);
             }
         }
-        eout[(size_t)k * n + i] = make_float4(eo.x, eo.y, eo.z, ho.x);
-        hout[(size_t)k * n + i] = make_float2(ho.y, ho.z);
+        hv_put<S>(a, k, i, make_float4(eo.x, eo.y, eo.z, ho.x), make_float2(ho.y, ho.z));
     });
 }
 
 // Equilibria for fields E, B and J = 0 (Appendix B initialisation), stored so that cell x pulls
 // them at the next step: direction i at y holds the equilibrium of cell y + v_i.
-template <int M>
+template <int S, int M>
 __global__ void __launch_bounds__(kBlock) hv_init_kernel(StepArgs a, const float* __restrict__ E,
                                                          const float* __restrict__ B) {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= a.g.n) return;
     const int n = a.g.n;
     const Neighbourhood h = neighbourhood(a.g, y);
-    float4* __restrict__ eout = static_cast<float4*>(a.fout);
-    float2* __restrict__ hout = static_cast<float2*>(a.fout2);
     static_for<0, 6>([&](auto ic) {
         constexpr int k = decltype(ic)::value;
-        constexpr int A = kHVAxis[k], S = kHVSign[k];
+        constexpr int A = kHVAxis[k], G = kHVSign[k];
         const int x = push_index<k>(h);
-        const float3 mat = load_material<M>(a.media, x);
-        const float eps = a.eps0 * mat.x, mu = a.mu0 * mat.y;
+        const MatCoef mat = load_coef<kModelHV, M>(a.media, x, a.eps0, a.mu0);
         const float3 Ex = make_float3(__ldg(&E[x]), __ldg(&E[n + x]), __ldg(&E[2 * n + x]));
         const float3 Bx = make_float3(__ldg(&B[x]), __ldg(&B[n + x]), __ldg(&B[2 * n + x]));
-        const float3 Hx = make_float3(Bx.x / mu, Bx.y / mu, Bx.z / mu);
-        const float3 cH = axis_cross<A, S>(Hx);
-        const float3 cE = axis_cross<A, S>(Ex);
+        const float3 cH = axis_cross<A, G>(hv_h(Bx, mat));
+        const float3 cE = axis_cross<A, G>(Ex);
+        const float3 d6 = hv_sixth_of_d(Ex, mat), b6 = sixth(Bx);
         // e^eq = (D - 3 v x B / mu) / 6 = D/6 - (v x H)/2;  h^eq = (B + 3 v x D / eps) / 6 = B/6 + (v x E)/2
-        eout[(size_t)k * n + y] = make_float4((eps * Ex.x) / 6.f - 0.5f * cH.x, (eps * Ex.y) / 6.f - 0.5f * cH.y,
-                                              (eps * Ex.z) / 6.f - 0.5f * cH.z, Bx.x / 6.f + 0.5f * cE.x);
-        hout[(size_t)k * n + y] = make_float2(Bx.y / 6.f + 0.5f * cE.y, Bx.z / 6.f + 0.5f * cE.z);
+        hv_put<S>(a, k, y,
+                  make_float4(d6.x - 0.5f * cH.x, d6.y - 0.5f * cH.y, d6.z - 0.5f * cH.z, b6.x + 0.5f * cE.x),
+                  make_float2(b6.y + 0.5f * cE.y, b6.z + 0.5f * cE.z));
     });
 }
 
-template <int M, bool kSpecial>
+template <int S, int M, bool kSpecial>
 __global__ void __launch_bounds__(kBlock) hv_fields_kernel(StepArgs a, FieldsOut out) {
     int i, m = 0;
     if constexpr (kSpecial) {
@@ -186,11 +207,11 @@ __global__ void __launch_bounds__(kBlock) hv_fields_kernel(StepArgs a, FieldsOut
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 e[6];
     float2 hy[6];
-    hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
-    const float3 mat = load_material<M>(a.media, i);
+    hv_pull<S>(a, h, e, hy);
+    const MatCoef mat = load_coef<kModelHV, M>(a.media, i, a.eps0, a.mu0);
     float3 jext = make_float3(0.f, 0.f, 0.f);
     if constexpr (kSpecial) jext = cell_source(a.sv, a.sc, m).J;
-    const HVFields F = hv_fields(e, hy, mat, a.eps0, a.mu0, jext);
+    const HVFields F = hv_fields(e, hy, mat, jext);
     auto put = [&](float* p, float3 v) {
         if (p) {
             p[i] = v.x;
@@ -206,6 +227,7 @@ __global__ void __launch_bounds__(kBlock) hv_fields_kernel(StepArgs a, FieldsOut
 }
 
 // Canonical layout out[k * n + x], k = r*18 + (i-1)*3 + c.
+template <int S>
 __global__ void __launch_bounds__(kBlock) hv_get_kernel(StepArgs a, float* __restrict__ out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.g.n) return;
@@ -213,7 +235,7 @@ __global__ void __launch_bounds__(kBlock) hv_get_kernel(StepArgs a, float* __res
     const Neighbourhood h = neighbourhood(a.g, x);
     float4 e[6];
     float2 hy[6];
-    hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
+    hv_pull<S>(a, h, e, hy);
     static_for<0, 6>([&](auto ic) {
         constexpr int k = decltype(ic)::value;
         out[(size_t)(3 * k + 0) * n + x] = e[k].x;
@@ -225,25 +247,25 @@ __global__ void __launch_bounds__(kBlock) hv_get_kernel(StepArgs a, float* __res
     });
 }
 
+template <int S>
 __global__ void __launch_bounds__(kBlock) hv_set_kernel(StepArgs a, const float* __restrict__ in) {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= a.g.n) return;
     const int n = a.g.n;
     const Neighbourhood h = neighbourhood(a.g, y);
-    float4* __restrict__ eout = static_cast<float4*>(a.fout);
-    float2* __restrict__ hout = static_cast<float2*>(a.fout2);
     static_for<0, 6>([&](auto ic) {
         constexpr int k = decltype(ic)::value;
         const int x = push_index<k>(h);
-        eout[(size_t)k * n + y] = make_float4(in[(size_t)(3 * k) * n + x], in[(size_t)(3 * k + 1) * n + x],
-                                              in[(size_t)(3 * k + 2) * n + x], in[(size_t)(18 + 3 * k) * n + x]);
-        hout[(size_t)k * n + y] = make_float2(in[(size_t)(19 + 3 * k) * n + x], in[(size_t)(20 + 3 * k) * n + x]);
+        hv_put<S>(a, k, y,
+                  make_float4(in[(size_t)(3 * k) * n + x], in[(size_t)(3 * k + 1) * n + x],
+                              in[(size_t)(3 * k + 2) * n + x], in[(size_t)(18 + 3 * k) * n + x]),
+                  make_float2(in[(size_t)(19 + 3 * k) * n + x], in[(size_t)(20 + 3 * k) * n + x]));
     });
 }
 
 // Per-block partial sums of (1/2)(E.D + B.H) and sum f^2 (E does not depend on J_ext in HV, so no
 // source-cell correction is needed).
-template <int M>
+template <int S, int M>
 __global__ void __launch_bounds__(kBlock) hv_reduce_kernel(StepArgs a, double* __restrict__ partials) {
     double w = 0.0, f2 = 0.0;
     const int n = a.g.n;
@@ -251,9 +273,9 @@ __global__ void __launch_bounds__(kBlock) hv_reduce_kernel(StepArgs a, double* _
         const Neighbourhood h = neighbourhood(a.g, i);
         float4 e[6];
         float2 hy[6];
-        hv_pull(static_cast<const float4*>(a.fin), static_cast<const float2*>(a.fin2), n, h, e, hy);
-        const float3 mat = load_material<M>(a.media, i);
-        const HVFields F = hv_fields(e, hy, mat, a.eps0, a.mu0, make_float3(0.f, 0.f, 0.f));
+        hv_pull<S>(a, h, e, hy);
+        const MatCoef mat = load_coef<kModelHV, M>(a.media, i, a.eps0, a.mu0);
+        const HVFields F = hv_fields(e, hy, mat, make_float3(0.f, 0.f, 0.f));
         w += 0.5 * ((double)F.E.x * F.D.x + (double)F.E.y * F.D.y + (double)F.E.z * F.D.z +
                     (double)F.B.x * F.H.x + (double)F.B.y * F.H.y + (double)F.B.z * F.H.z);
         double s = 0.0;
@@ -266,70 +288,73 @@ __global__ void __launch_bounds__(kBlock) hv_reduce_kernel(StepArgs a, double* _
     block_sum3_store(w, f2, 0.0, partials + 3 * blockIdx.x);
 }
 
-inline int blocks_for(int n) { return (n + kBlock - 1) / kBlock; }
-
 }  // namespace
 
 int hv_launch_step(const StepArgs& a, cudaStream_t st) {
-    const int nb = blocks_for(a.g.n);
-    switch (a.media_mode) {
-        case kUniform: hv_step_kernel<kUniform, false><<<nb, kBlock, 0, st>>>(a); break;
-        case kTable: hv_step_kernel<kTable, false><<<nb, kBlock, 0, st>>>(a); break;
-        default: hv_step_kernel<kPerCell, false><<<nb, kBlock, 0, st>>>(a); break;
-    }
-    if (a.sv.n_special == 0) return 1;
-    const int ns = blocks_for(a.sv.n_special);
-    switch (a.media_mode) {
-        case kUniform: hv_step_kernel<kUniform, true><<<ns, kBlock, 0, st>>>(a); break;
-        case kTable: hv_step_kernel<kTable, true><<<ns, kBlock, 0, st>>>(a); break;
-        default: hv_step_kernel<kPerCell, true><<<ns, kBlock, 0, st>>>(a); break;
-    }
-    return 2;
+    int launched = 0;
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            hv_step_kernel<S, M, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+            launched = 1;
+            if (a.sv.n_special > 0) {
+                hv_step_kernel<S, M, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
+                launched = 2;
+            }
+        });
+    });
+    return launched;
 }
 
 int hv_launch_init(const StepArgs& a, const float* E, const float* B, cudaStream_t st) {
-    const int nb = blocks_for(a.g.n);
-    switch (a.media_mode) {
-        case kUniform: hv_init_kernel<kUniform><<<nb, kBlock, 0, st>>>(a, E, B); break;
-        case kTable: hv_init_kernel<kTable><<<nb, kBlock, 0, st>>>(a, E, B); break;
-        default: hv_init_kernel<kPerCell><<<nb, kBlock, 0, st>>>(a, E, B); break;
-    }
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            hv_init_kernel<S, M><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, E, B);
+        });
+    });
     return 1;
 }
 
 int hv_launch_fields(const StepArgs& a, FieldsOut out, cudaStream_t st) {
-    const int nb = blocks_for(a.g.n);
-    switch (a.media_mode) {
-        case kUniform: hv_fields_kernel<kUniform, false><<<nb, kBlock, 0, st>>>(a, out); break;
-        case kTable: hv_fields_kernel<kTable, false><<<nb, kBlock, 0, st>>>(a, out); break;
-        default: hv_fields_kernel<kPerCell, false><<<nb, kBlock, 0, st>>>(a, out); break;
-    }
-    if (a.sv.n_special == 0) return 1;
-    const int ns = blocks_for(a.sv.n_special);
-    switch (a.media_mode) {
-        case kUniform: hv_fields_kernel<kUniform, true><<<ns, kBlock, 0, st>>>(a, out); break;
-        case kTable: hv_fields_kernel<kTable, true><<<ns, kBlock, 0, st>>>(a, out); break;
-        default: hv_fields_kernel<kPerCell, true><<<ns, kBlock, 0, st>>>(a, out); break;
-    }
-    return 2;
+    int launched = 0;
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            hv_fields_kernel<S, M, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, out);
+            launched = 1;
+            if (a.sv.n_special > 0) {
+                hv_fields_kernel<S, M, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a, out);
+                launched = 2;
+            }
+        });
+    });
+    return launched;
 }
 
 int hv_launch_get(const StepArgs& a, float* out, cudaStream_t st) {
-    hv_get_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, out);
+    with_storage(a.storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        hv_get_kernel<S><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, out);
+    });
     return 1;
 }
 
 int hv_launch_set(const StepArgs& a, const float* in, cudaStream_t st) {
-    hv_set_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, in);
+    with_storage(a.storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        hv_set_kernel<S><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, in);
+    });
     return 1;
 }
 
 int hv_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* result, cudaStream_t st) {
-    switch (a.media_mode) {
-        case kUniform: hv_reduce_kernel<kUniform><<<n_blocks, kBlock, 0, st>>>(a, partials); break;
-        case kTable: hv_reduce_kernel<kTable><<<n_blocks, kBlock, 0, st>>>(a, partials); break;
-        default: hv_reduce_kernel<kPerCell><<<n_blocks, kBlock, 0, st>>>(a, partials); break;
-    }
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            hv_reduce_kernel<S, M><<<n_blocks, kBlock, 0, st>>>(a, partials);
+        });
+    });
     return 1 + launch_reduce_partials(partials, n_blocks, result, st);
 }
 

@@ -12,6 +12,8 @@
 // vector load per group.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,17 +26,35 @@ constexpr int kBlock = 256;
 
 enum MediaMode { kUniform = 0, kTable = 1, kPerCell = 2 };
 
+// Population storage. Arithmetic is FP32 in every case; 16-bit storage converts at the pull and the
+// store. A stored 16-bit value is f * scale (scale a power of two, so the scaling itself is exact).
+enum StorageKind { kF32 = 0, kBF16 = 1, kF16 = 2 };
+
+// Lattice shape. Cell coordinates come from the linear index by multiplication with host-computed
+// magic numbers (Granlund and Montgomery, "Division by invariant integers using multiplication"):
+// floor(i / d) = (i * M) >> (32 + k) with k = ceil(log2 d), M = ceil(2^(32+k) / d), exact for every
+// i < 2^31.
 struct Geometry {
     int nx, ny, nz;
     int n;  // nx * ny * nz, < 2^31
+    unsigned long long mx, mxy;  // magic multipliers for division by nx and by nx * ny
+    int kx, kxy;
 };
 
-// Media as the kernels see it; (eps_r, mu_r, sigma) per cell.
+// Per-material coefficients, computed on the host in double precision and rounded once (reciprocals
+// as RN(1/d) of the stored float d, so that div_rn below is exact).
+//   MM: c0 = (eps_r, 1/eps_r, g = 1/(1 + mu0 sigma/(4 eps_r)), 1/(4 mu_r)),  c1 = (sigma, mu_r, 0, 0)
+//   HV: c0 = (eps, 1/eps, mu, 1/mu) with eps = eps0 eps_r, mu = mu0 mu_r,   c1 = (sigma, eps_r, 0, 0)
+struct MatCoef {
+    float4 c0, c1;
+};
+
+// Media as the kernels see them.
 struct MediaView {
-    float4 uniform;          // kUniform: (eps_r, mu_r, sigma, 0)
+    MatCoef uniform;         // kUniform
     const uint8_t* id;       // kTable: material id per cell
-    const float4* table;     // kTable: (eps_r, mu_r, sigma, 0) per material
-    const float* eps_r;      // kPerCell
+    const MatCoef* table;    // kTable: coefficients per material
+    const float* eps_r;      // kPerCell: raw values; coefficients are formed per cell
     const float* mu_r;
     const float* sigma;
 };
@@ -69,6 +89,9 @@ struct StepArgs {
     SourceView sv;
     SourceScalars sc;
     float eps0, mu0;
+    int storage;      // StorageKind
+    float scale;      // 16-bit storage: stored = f * scale
+    float inv_scale;  // 1 / scale
 };
 
 // Field output: for each selected field a 3 x n block; null pointers are skipped.
@@ -79,6 +102,101 @@ struct FieldsOut {
     float* H;
     float* J;
 };
+
+// --- population storage traits -----------------------------------------------------------
+// Pack4<S>: four populations (one MM direction group, or HV's e_x, e_y, e_z, h_x) as one vector;
+// Pack2<S>: two populations (HV's h_y, h_z). FP32: float4 / float2; 16-bit: 8 / 4 bytes.
+template <int S>
+struct Pack4;
+template <int S>
+struct Pack2;
+
+template <>
+struct Pack4<kF32> {
+    using T = float4;
+    __device__ static float4 load(const T* p, float) { return __ldg(p); }
+    __device__ static T pack(float4 v, float) { return v; }
+};
+template <>
+struct Pack2<kF32> {
+    using T = float2;
+    __device__ static float2 load(const T* p, float) { return __ldg(p); }
+    __device__ static T pack(float2 v, float) { return v; }
+};
+
+template <>
+struct Pack4<kF16> {
+    using T = uint2;
+    __device__ static float4 load(const T* p, float inv) {
+        const uint2 u = __ldg(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return make_float4(a.x * inv, a.y * inv, b.x * inv, b.y * inv);
+    }
+    __device__ static T pack(float4 v, float scale) {
+        const __half2 a = __floats2half2_rn(v.x * scale, v.y * scale);
+        const __half2 b = __floats2half2_rn(v.z * scale, v.w * scale);
+        return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+    }
+};
+template <>
+struct Pack2<kF16> {
+    using T = uint32_t;
+    __device__ static float2 load(const T* p, float inv) {
+        const uint32_t u = __ldg(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u));
+        return make_float2(a.x * inv, a.y * inv);
+    }
+    __device__ static T pack(float2 v, float scale) {
+        const __half2 a = __floats2half2_rn(v.x * scale, v.y * scale);
+        return *reinterpret_cast<const uint32_t*>(&a);
+    }
+};
+
+template <>
+struct Pack4<kBF16> {
+    using T = uint2;
+    __device__ static float4 load(const T* p, float inv) {
+        const uint2 u = __ldg(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        return make_float4(a.x * inv, a.y * inv, b.x * inv, b.y * inv);
+    }
+    __device__ static T pack(float4 v, float scale) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x * scale, v.y * scale);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v.z * scale, v.w * scale);
+        return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+    }
+};
+template <>
+struct Pack2<kBF16> {
+    using T = uint32_t;
+    __device__ static float2 load(const T* p, float inv) {
+        const uint32_t u = __ldg(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+        return make_float2(a.x * inv, a.y * inv);
+    }
+    __device__ static T pack(float2 v, float scale) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x * scale, v.y * scale);
+        return *reinterpret_cast<const uint32_t*>(&a);
+    }
+};
+
+// Host-side dispatch of a runtime storage kind / media mode to a compile-time constant.
+template <class F>
+inline void with_storage(int s, F&& f) {
+    if (s == kBF16) f(std::integral_constant<int, kBF16>{});
+    else if (s == kF16) f(std::integral_constant<int, kF16>{});
+    else f(std::integral_constant<int, kF32>{});
+}
+template <class F>
+inline void with_media(int m, F&& f) {
+    if (m == kTable) f(std::integral_constant<int, kTable>{});
+    else if (m == kPerCell) f(std::integral_constant<int, kPerCell>{});
+    else f(std::integral_constant<int, kUniform>{});
+}
+
+inline int blocks_for(int n) { return (n + kBlock - 1) / kBlock; }
 
 // --- compile-time loop ---------------------------------------------------------------------
 template <int I, int N, class F>
@@ -117,9 +235,9 @@ struct Neighbourhood {
 
 __device__ __forceinline__ Neighbourhood neighbourhood(const Geometry& g, int i) {
     const int nxy = g.nx * g.ny;
-    const int z = i / nxy;
+    const int z = (int)(((unsigned long long)(unsigned)i * g.mxy) >> (32 + g.kxy));
     const int r = i - z * nxy;
-    const int y = r / g.nx;
+    const int y = (int)(((unsigned long long)(unsigned)r * g.mx) >> (32 + g.kx));
     const int x = r - y * g.nx;
     Neighbourhood h;
     h.xo[0] = x == 0 ? g.nx - 1 : x - 1;
@@ -142,15 +260,41 @@ __device__ __forceinline__ int shifted(const Neighbourhood& h) {
     return h.xo[SX + 1] + h.yo[SY + 1] + h.zo[SZ + 1];
 }
 
-template <int M>
-__device__ __forceinline__ float3 load_material(const MediaView& m, int i) {
+// x / d rounded to nearest, from r = RN(1/d): q = RN(x r), e = x - q d (exact with a fused
+// multiply-add), result RN(q + e r). By Markstein's theorem on FMA-based division this is the
+// correctly rounded quotient (away from underflow and overflow), without a divide instruction or
+// its special-case branch.
+__device__ __forceinline__ float div_rn(float x, float d, float r) {
+    const float q = __fmul_rn(x, r);
+    const float e = __fmaf_rn(-q, d, x);
+    return __fmaf_rn(e, r, q);
+}
+
+enum ModelKind { kModelMM = 0, kModelHV = 1 };
+
+// Coefficients of cell i. Per-cell media form them here from the raw values (true divisions).
+template <int Model, int M>
+__device__ __forceinline__ MatCoef load_coef(const MediaView& m, int i, float eps0, float mu0) {
     if constexpr (M == kUniform) {
-        return make_float3(m.uniform.x, m.uniform.y, m.uniform.z);
+        return m.uniform;
     } else if constexpr (M == kTable) {
-        const float4 t = __ldg(&m.table[__ldg(&m.id[i])]);
-        return make_float3(t.x, t.y, t.z);
+        const MatCoef* t = &m.table[__ldg(&m.id[i])];
+        MatCoef c;
+        c.c0 = __ldg(&t->c0);
+        c.c1 = __ldg(&t->c1);
+        return c;
     } else {
-        return make_float3(__ldg(&m.eps_r[i]), __ldg(&m.mu_r[i]), __ldg(&m.sigma[i]));
+        const float er = __ldg(&m.eps_r[i]), mr = __ldg(&m.mu_r[i]), sg = __ldg(&m.sigma[i]);
+        MatCoef c;
+        if constexpr (Model == kModelMM) {
+            c.c0 = make_float4(er, 1.f / er, 1.f / (1.f + 0.5f * (sg / er)), 0.25f / mr);
+            c.c1 = make_float4(sg, mr, 0.f, 0.f);
+        } else {
+            const float eps = eps0 * er, mu = mu0 * mr;
+            c.c0 = make_float4(eps, 1.f / eps, mu, 1.f / mu);
+            c.c1 = make_float4(sg, er, 0.f, 0.f);
+        }
+        return c;
     }
 }
 

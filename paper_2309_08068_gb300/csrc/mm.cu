@@ -1,8 +1,9 @@
 // Mendoza-Munoz (MM) model kernels, arXiv 2309.08068 Section II.
 //
-// One thread updates one cell. The 48 moving populations arrive as 12 float4 pulls (one per
-// D3Q13 velocity; the four values of a velocity move together), the whole collision runs in
-// registers, and the 12 float4 results are stored at the cell (pull scheme). Sources and imposed
+// One thread updates one cell. The 48 moving populations arrive as 12 vector pulls (one per D3Q13
+// velocity; the four values of a velocity move together: a float4, or 8 bytes with 16-bit storage),
+// the whole collision runs in FP32 registers, and the 12 results are stored at the cell (pull
+// scheme). Sources and imposed
 // cells are handled by a second, small launch over the merged source-cell list that recomputes
 // those cells with their current and imposed fields and overwrites them; the main launch stays
 // branch-free.
@@ -81,7 +82,7 @@ __device__ __forceinline__ float moment_component(const float (&x)[12]) {
 }
 
 template <bool kRho>
-__device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0, float3 mat, float3 jext) {
+__device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0, const MatCoef& mat, float3 jext) {
     float de[12], db[12];
     float rho = rest0;
     static_for<0, 12>([&](auto dc) {
@@ -95,34 +96,42 @@ __device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0
     const float bx = moment_component<kMMB, 0, 4>(db), by = moment_component<kMMB, 1, 4>(db),
                 bz = moment_component<kMMB, 2, 4>(db);
     MMFields o;
-    const float g = 1.f / (1.f + 0.5f * (mat.z / mat.x));
+    const float g = mat.c0.z;  // 1 / (1 + mu0 sigma / (4 eps_r))
+    const float er = mat.c0.x, inv_er = mat.c0.y, sigma = mat.c1.x;
     o.Dpp.x = (0.5f * dx - 0.5f * jext.x) * g;
     o.Dpp.y = (0.5f * dy - 0.5f * jext.y) * g;
     o.Dpp.z = (0.5f * dz - 0.5f * jext.z) * g;
-    o.E.x = o.Dpp.x / mat.x;
-    o.E.y = o.Dpp.y / mat.x;
-    o.E.z = o.Dpp.z / mat.x;
+    o.E.x = div_rn(o.Dpp.x, er, inv_er);
+    o.E.y = div_rn(o.Dpp.y, er, inv_er);
+    o.E.z = div_rn(o.Dpp.z, er, inv_er);
     o.B = make_float3(bx, by, bz);
-    o.J.x = mat.z * o.E.x + jext.x;
-    o.J.y = mat.z * o.E.y + jext.y;
-    o.J.z = mat.z * o.E.z + jext.z;
+    o.J.x = sigma * o.E.x + jext.x;
+    o.J.y = sigma * o.E.y + jext.y;
+    o.J.z = sigma * o.E.z + jext.z;
     o.rho = rho;
-    o.inv4mu = 0.25f / mat.y;
+    o.inv4mu = mat.c0.w;
     return o;
 }
 
 // Pull the 12 groups of cell i from the previous step's buffer: direction d from cell i - v_d.
-__device__ __forceinline__ void mm_pull(const float4* __restrict__ fin, int n, const Neighbourhood& h,
-                                        float4 (&f)[12]) {
+template <int S>
+__device__ __forceinline__ void mm_pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) {
+    const auto* __restrict__ fin = static_cast<const typename Pack4<S>::T*>(a.fin);
     static_for<0, 12>([&](auto dc) {
         constexpr int d = decltype(dc)::value;
         const int src = shifted<-kMMV[d][0], -kMMV[d][1], -kMMV[d][2]>(h);
-        f[d] = __ldg(fin + (size_t)d * n + src);
+        f[d] = Pack4<S>::load(fin + (size_t)d * a.g.n + src, a.inv_scale);
     });
 }
 
-template <int M, bool kSpecial, bool kRho>
-__global__ void __launch_bounds__(kBlock) mm_step_kernel(StepArgs a) {
+template <int S>
+__device__ __forceinline__ void mm_put(const StepArgs& a, int d, int i, float4 v) {
+    auto* __restrict__ fout = static_cast<typename Pack4<S>::T*>(a.fout);
+    fout[(size_t)d * a.g.n + i] = Pack4<S>::pack(v, a.scale);
+}
+
+template <int S, int M, bool kSpecial, bool kRho>
+__global__ void __launch_bounds__(kBlock, 3) mm_step_kernel(StepArgs a) {
     int i, m = 0;
     if constexpr (kSpecial) {
         m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -132,13 +141,10 @@ __global__ void __launch_bounds__(kBlock) mm_step_kernel(StepArgs a) {
         i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i >= a.g.n) return;
     }
-    const int n = a.g.n;
-    const float4* __restrict__ fin = static_cast<const float4*>(a.fin);
-    float4* __restrict__ fout = static_cast<float4*>(a.fout);
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 f[12];
-    mm_pull(fin, n, h, f);
-    const float3 mat = load_material<M>(a.media, i);
+    mm_pull<S>(a, h, f);
+    const MatCoef mat = load_coef<kModelMM, M>(a.media, i, a.eps0, a.mu0);
     float rest0 = 0.f;
     if constexpr (kRho) rest0 = a.rho_in[i];
     CellSource cs;
@@ -166,24 +172,23 @@ __global__ void __launch_bounds__(kBlock) mm_step_kernel(StepArgs a) {
             if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
                 const float bi = sdot<b0, b1, b2>(cs.B.x, cs.B.y, cs.B.z);
                 const float ee = sdot<e0, e1, e2>(cs.E.x, cs.E.y, cs.E.z);
-                const float alpha = 0.125f * (mat.x * ee) + 0.5f * bi * F.inv4mu;
+                const float alpha = 0.125f * (mat.c0.x * ee) + 0.5f * bi * F.inv4mu;
                 const float beta = 0.125f * ee + 0.125f * bi;
                 o = make_float4(alpha, -alpha, beta, -beta);
             }
         }
-        fout[(size_t)d * n + i] = o;
+        mm_put<S>(a, d, i, o);
     });
     if constexpr (kRho) a.rho_out[i] = 2.f * F.rho - rest0;  // f_0^(0)eq = rho_c; stays in place
 }
 
 // Equilibrium populations of cell x for fields E, B and J = 0 (Appendix B initialisation).
-template <int M>
+template <int S, int M>
 __global__ void __launch_bounds__(kBlock) mm_init_kernel(StepArgs a, const float* __restrict__ E,
                                                          const float* __restrict__ B) {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= a.g.n) return;
     const int n = a.g.n;
-    float4* __restrict__ fout = static_cast<float4*>(a.fout);
     const Neighbourhood h = neighbourhood(a.g, y);
     // Stored value at y for direction d is the population cell x = y + v_d pulls next step.
     static_for<0, 12>([&](auto dc) {
@@ -191,16 +196,16 @@ __global__ void __launch_bounds__(kBlock) mm_init_kernel(StepArgs a, const float
         constexpr int e0 = kMMEh[d][0], e1 = kMMEh[d][1], e2 = kMMEh[d][2];
         constexpr int b0 = kMMB[d][0], b1 = kMMB[d][1], b2 = kMMB[d][2];
         const int x = shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h);
-        const float3 mat = load_material<M>(a.media, x);
+        const MatCoef mat = load_coef<kModelMM, M>(a.media, x, a.eps0, a.mu0);
         const float ee = sdot<e0, e1, e2>(__ldg(&E[x]), __ldg(&E[n + x]), __ldg(&E[2 * n + x]));
         const float bb = sdot<b0, b1, b2>(__ldg(&B[x]), __ldg(&B[n + x]), __ldg(&B[2 * n + x]));
-        const float alpha = 0.125f * (mat.x * ee) + bb * (0.125f / mat.y);
+        const float alpha = 0.125f * (mat.c0.x * ee) + bb * (0.5f * mat.c0.w);  // 0.5 / (4 mu_r)
         const float beta = 0.125f * ee + 0.125f * bb;
-        fout[(size_t)d * n + y] = make_float4(alpha, -alpha, beta, -beta);
+        mm_put<S>(a, d, y, make_float4(alpha, -alpha, beta, -beta));
     });
 }
 
-template <int M, bool kSpecial, bool kRho>
+template <int S, int M, bool kSpecial>
 __global__ void __launch_bounds__(kBlock) mm_fields_kernel(StepArgs a, FieldsOut out) {
     int i, m = 0;
     if constexpr (kSpecial) {
@@ -214,8 +219,8 @@ __global__ void __launch_bounds__(kBlock) mm_fields_kernel(StepArgs a, FieldsOut
     const int n = a.g.n;
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 f[12];
-    mm_pull(static_cast<const float4*>(a.fin), n, h, f);
-    const float3 mat = load_material<M>(a.media, i);
+    mm_pull<S>(a, h, f);
+    const MatCoef mat = load_coef<kModelMM, M>(a.media, i, a.eps0, a.mu0);
     float3 jext = make_float3(0.f, 0.f, 0.f);
     if constexpr (kSpecial) jext = cell_source(a.sv, a.sc, m).J;
     const MMFields F = mm_fields<false>(f, 0.f, mat, jext);
@@ -229,12 +234,15 @@ __global__ void __launch_bounds__(kBlock) mm_fields_kernel(StepArgs a, FieldsOut
     put(out.E, F.E);
     put(out.B, F.B);
     put(out.D, F.Dpp);  // D = eps0 eps_r E with eps0 = 1
-    const float inv2mu = 1.f / (2.f * mat.y);  // H = B / (mu0 mu_r), mu0 = 2
-    put(out.H, make_float3(F.B.x * inv2mu, F.B.y * inv2mu, F.B.z * inv2mu));
+    // H = B / (mu0 mu_r) with mu0 = 2; 1 / (2 mu_r) = 2 / (4 mu_r) exactly
+    const float two_mu = 2.f * mat.c1.y, inv2mu = 2.f * mat.c0.w;
+    put(out.H, make_float3(div_rn(F.B.x, two_mu, inv2mu), div_rn(F.B.y, two_mu, inv2mu),
+                           div_rn(F.B.z, two_mu, inv2mu)));
     put(out.J, F.J);
 }
 
 // Canonical layout out[k * n + x]: k = r*24 + p*8 + (i-1)*2 + j = r*24 + 2d + j; 48, 49 rest.
+template <int S>
 __global__ void __launch_bounds__(kBlock) mm_get_kernel(StepArgs a, const float* __restrict__ rest1,
                                                         float* __restrict__ out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(kBlock) mm_get_kernel(StepArgs a, const float*
     const int n = a.g.n;
     const Neighbourhood h = neighbourhood(a.g, x);
     float4 f[12];
-    mm_pull(static_cast<const float4*>(a.fin), n, h, f);
+    mm_pull<S>(a, h, f);
     static_for<0, 12>([&](auto dc) {
         constexpr int d = decltype(dc)::value;
         out[(size_t)(2 * d) * n + x] = f[d].x;
@@ -254,18 +262,19 @@ __global__ void __launch_bounds__(kBlock) mm_get_kernel(StepArgs a, const float*
     out[(size_t)49 * n + x] = rest1 ? rest1[x] : 0.f;
 }
 
+template <int S>
 __global__ void __launch_bounds__(kBlock) mm_set_kernel(StepArgs a, const float* __restrict__ in,
                                                         float* __restrict__ rest1) {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= a.g.n) return;
     const int n = a.g.n;
-    float4* __restrict__ fout = static_cast<float4*>(a.fout);
     const Neighbourhood h = neighbourhood(a.g, y);
     static_for<0, 12>([&](auto dc) {
         constexpr int d = decltype(dc)::value;
         const int x = shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h);
-        fout[(size_t)d * n + y] = make_float4(in[(size_t)(2 * d) * n + x], in[(size_t)(2 * d + 1) * n + x],
-                                              in[(size_t)(24 + 2 * d) * n + x], in[(size_t)(25 + 2 * d) * n + x]);
+        mm_put<S>(a, d, y,
+                  make_float4(in[(size_t)(2 * d) * n + x], in[(size_t)(2 * d + 1) * n + x],
+                              in[(size_t)(24 + 2 * d) * n + x], in[(size_t)(25 + 2 * d) * n + x]));
     });
     if (a.rho_out) a.rho_out[y] = in[(size_t)48 * n + y];
     if (rest1) rest1[y] = in[(size_t)49 * n + y];
@@ -273,7 +282,7 @@ __global__ void __launch_bounds__(kBlock) mm_set_kernel(StepArgs a, const float*
 
 // Per-block partial sums of (1/2)(E.D + B.H), sum f^2 and rho_c over a grid-stride range of cells
 // (external current taken as zero here; the special-cell pass adds the correction).
-template <int M, bool kRho>
+template <int S, int M, bool kRho>
 __global__ void __launch_bounds__(kBlock) mm_reduce_kernel(StepArgs a, const float* __restrict__ rest1,
                                                            double* __restrict__ partials) {
     double w = 0.0, f2 = 0.0, q = 0.0;
@@ -281,12 +290,12 @@ __global__ void __launch_bounds__(kBlock) mm_reduce_kernel(StepArgs a, const flo
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Neighbourhood h = neighbourhood(a.g, i);
         float4 f[12];
-        mm_pull(static_cast<const float4*>(a.fin), n, h, f);
-        const float3 mat = load_material<M>(a.media, i);
+        mm_pull<S>(a, h, f);
+        const MatCoef mat = load_coef<kModelMM, M>(a.media, i, a.eps0, a.mu0);
         float rest0 = 0.f;
         if constexpr (kRho) rest0 = a.rho_in[i];
         const MMFields F = mm_fields<kRho>(f, rest0, mat, make_float3(0.f, 0.f, 0.f));
-        const double inv2mu = 1.0 / (2.0 * (double)mat.y);
+        const double inv2mu = 1.0 / (2.0 * (double)mat.c1.y);
         w += 0.5 * ((double)F.E.x * F.Dpp.x + (double)F.E.y * F.Dpp.y + (double)F.E.z * F.Dpp.z) +
              0.5 * inv2mu * ((double)F.B.x * F.B.x + (double)F.B.y * F.B.y + (double)F.B.z * F.B.z);
         double s = 0.0;
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(kBlock) mm_reduce_kernel(StepArgs a, const flo
 }
 
 // Energy correction at source cells: (energy with J_ext) - (energy with J_ext = 0).
-template <int M>
+template <int S, int M>
 __global__ void __launch_bounds__(kBlock) mm_reduce_special_kernel(StepArgs a, double* __restrict__ partials) {
     double w = 0.0;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,8 +322,8 @@ __global__ void __launch_bounds__(kBlock) mm_reduce_special_kernel(StepArgs a, d
         const int i = a.sv.cell[m];
         const Neighbourhood h = neighbourhood(a.g, i);
         float4 f[12];
-        mm_pull(static_cast<const float4*>(a.fin), a.g.n, h, f);
-        const float3 mat = load_material<M>(a.media, i);
+        mm_pull<S>(a, h, f);
+        const MatCoef mat = load_coef<kModelMM, M>(a.media, i, a.eps0, a.mu0);
         const MMFields F1 = mm_fields<false>(f, 0.f, mat, cell_source(a.sv, a.sc, m).J);
         const MMFields F0 = mm_fields<false>(f, 0.f, mat, make_float3(0.f, 0.f, 0.f));
         w = 0.5 * ((double)F1.E.x * F1.Dpp.x + (double)F1.E.y * F1.Dpp.y + (double)F1.E.z * F1.Dpp.z) -
@@ -323,102 +332,88 @@ __global__ void __launch_bounds__(kBlock) mm_reduce_special_kernel(StepArgs a, d
     block_sum3_store(w, 0.0, 0.0, partials + 3 * blockIdx.x);
 }
 
-inline int blocks_for(int n) { return (n + kBlock - 1) / kBlock; }
-
 }  // namespace
 
 int mm_launch_step(const StepArgs& a, cudaStream_t st) {
     const bool rho = a.rho_in != nullptr;
-    const int nb = blocks_for(a.g.n);
-#define MM_STEP(M, S, R, NB) mm_step_kernel<M, S, R><<<NB, kBlock, 0, st>>>(a)
-    int launched = 1;
-    switch (a.media_mode) {
-        case kUniform: rho ? MM_STEP(kUniform, false, true, nb) : MM_STEP(kUniform, false, false, nb); break;
-        case kTable: rho ? MM_STEP(kTable, false, true, nb) : MM_STEP(kTable, false, false, nb); break;
-        default: rho ? MM_STEP(kPerCell, false, true, nb) : MM_STEP(kPerCell, false, false, nb); break;
-    }
-    if (a.sv.n_special > 0) {
-        const int ns = blocks_for(a.sv.n_special);
-        switch (a.media_mode) {
-            case kUniform: rho ? MM_STEP(kUniform, true, true, ns) : MM_STEP(kUniform, true, false, ns); break;
-            case kTable: rho ? MM_STEP(kTable, true, true, ns) : MM_STEP(kTable, true, false, ns); break;
-            default: rho ? MM_STEP(kPerCell, true, true, ns) : MM_STEP(kPerCell, true, false, ns); break;
-        }
-        ++launched;
-    }
-#undef MM_STEP
+    int launched = 0;
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            const int nb = blocks_for(a.g.n);
+            if (rho) mm_step_kernel<S, M, false, true><<<nb, kBlock, 0, st>>>(a);
+            else mm_step_kernel<S, M, false, false><<<nb, kBlock, 0, st>>>(a);
+            launched = 1;
+            if (a.sv.n_special > 0) {
+                const int ns = blocks_for(a.sv.n_special);
+                if (rho) mm_step_kernel<S, M, true, true><<<ns, kBlock, 0, st>>>(a);
+                else mm_step_kernel<S, M, true, false><<<ns, kBlock, 0, st>>>(a);
+                launched = 2;
+            }
+        });
+    });
     return launched;
 }
 
 int mm_launch_init(const StepArgs& a, const float* E, const float* B, cudaStream_t st) {
-    const int nb = blocks_for(a.g.n);
-    switch (a.media_mode) {
-        case kUniform: mm_init_kernel<kUniform><<<nb, kBlock, 0, st>>>(a, E, B); break;
-        case kTable: mm_init_kernel<kTable><<<nb, kBlock, 0, st>>>(a, E, B); break;
-        default: mm_init_kernel<kPerCell><<<nb, kBlock, 0, st>>>(a, E, B); break;
-    }
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            mm_init_kernel<S, M><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, E, B);
+        });
+    });
     return 1;
 }
 
 int mm_launch_fields(const StepArgs& a, FieldsOut out, cudaStream_t st) {
-    const int nb = blocks_for(a.g.n);
-    int launched = 1;
-    switch (a.media_mode) {
-        case kUniform: mm_fields_kernel<kUniform, false, false><<<nb, kBlock, 0, st>>>(a, out); break;
-        case kTable: mm_fields_kernel<kTable, false, false><<<nb, kBlock, 0, st>>>(a, out); break;
-        default: mm_fields_kernel<kPerCell, false, false><<<nb, kBlock, 0, st>>>(a, out); break;
-    }
-    if (a.sv.n_special > 0) {
-        const int ns = blocks_for(a.sv.n_special);
-        switch (a.media_mode) {
-            case kUniform: mm_fields_kernel<kUniform, true, false><<<ns, kBlock, 0, st>>>(a, out); break;
-            case kTable: mm_fields_kernel<kTable, true, false><<<ns, kBlock, 0, st>>>(a, out); break;
-            default: mm_fields_kernel<kPerCell, true, false><<<ns, kBlock, 0, st>>>(a, out); break;
-        }
-        ++launched;
-    }
+    int launched = 0;
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            mm_fields_kernel<S, M, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, out);
+            launched = 1;
+            if (a.sv.n_special > 0) {
+                mm_fields_kernel<S, M, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a, out);
+                launched = 2;
+            }
+        });
+    });
     return launched;
 }
 
 int mm_launch_get(const StepArgs& a, float* out, cudaStream_t st) {
-    mm_get_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, static_cast<const float*>(a.fin2), out);
+    with_storage(a.storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        mm_get_kernel<S><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, static_cast<const float*>(a.fin2), out);
+    });
     return 1;
 }
 
 int mm_launch_set(const StepArgs& a, const float* in, cudaStream_t st) {
-    mm_set_kernel<<<blocks_for(a.g.n), kBlock, 0, st>>>(a, in, static_cast<float*>(a.fout2));
+    with_storage(a.storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        mm_set_kernel<S><<<blocks_for(a.g.n), kBlock, 0, st>>>(a, in, static_cast<float*>(a.fout2));
+    });
     return 1;
 }
 
 int mm_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* result, cudaStream_t st) {
     const bool rho = a.rho_in != nullptr;
     const float* rest1 = static_cast<const float*>(a.fin2);
-    switch (a.media_mode) {
-        case kUniform:
-            rho ? mm_reduce_kernel<kUniform, true><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials)
-                : mm_reduce_kernel<kUniform, false><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
-            break;
-        case kTable:
-            rho ? mm_reduce_kernel<kTable, true><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials)
-                : mm_reduce_kernel<kTable, false><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
-            break;
-        default:
-            rho ? mm_reduce_kernel<kPerCell, true><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials)
-                : mm_reduce_kernel<kPerCell, false><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
-            break;
-    }
     int total = n_blocks, launched = 1;
-    if (a.sv.n_special > 0) {
-        const int ns = blocks_for(a.sv.n_special);
-        double* p2 = partials + 3 * n_blocks;
-        switch (a.media_mode) {
-            case kUniform: mm_reduce_special_kernel<kUniform><<<ns, kBlock, 0, st>>>(a, p2); break;
-            case kTable: mm_reduce_special_kernel<kTable><<<ns, kBlock, 0, st>>>(a, p2); break;
-            default: mm_reduce_special_kernel<kPerCell><<<ns, kBlock, 0, st>>>(a, p2); break;
-        }
-        total += ns;
-        ++launched;
-    }
+    with_storage(a.storage, [&](auto sc) {
+        with_media(a.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            if (rho) mm_reduce_kernel<S, M, true><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
+            else mm_reduce_kernel<S, M, false><<<n_blocks, kBlock, 0, st>>>(a, rest1, partials);
+            if (a.sv.n_special > 0) {
+                const int ns = blocks_for(a.sv.n_special);
+                mm_reduce_special_kernel<S, M><<<ns, kBlock, 0, st>>>(a, partials + 3 * n_blocks);
+                total += ns;
+                ++launched;
+            }
+        });
+    });
     return launched + launch_reduce_partials(partials, total, result, st);
 }
 

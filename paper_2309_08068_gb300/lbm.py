@@ -39,7 +39,10 @@ class _Media(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("track_rho", ctypes.c_int),
-                ("eps0", ctypes.c_double), ("mu0", ctypes.c_double)]
+                ("eps0", ctypes.c_double), ("mu0", ctypes.c_double), ("storage_scale", ctypes.c_double)]
+
+
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 
 
 class _TimeFn(ctypes.Structure):
@@ -124,7 +127,7 @@ class Lattice:
     """
 
     def __init__(self, model: str, shape, eps_r=None, mu_r=None, sigma=None, *, track_rho: bool = False,
-                 eps0: float = 0.0, mu0: float = 0.0, stream=None):
+                 eps0: float = 0.0, mu0: float = 0.0, stream=None, storage: str = "f32", storage_scale: float = 0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Lattice needs a CUDA device; there is no CPU fallback")
@@ -149,7 +152,9 @@ class Lattice:
         if len(on_dev) > 1:
             raise ValueError("media arrays must all be host or all device arrays")
         media.on_device = on_dev.pop() if on_dev else 0
-        opts = _Options(0, ctypes.c_void_p(self.stream.cuda_stream), int(track_rho), float(eps0), float(mu0))
+        opts = _Options(STORAGE[storage], ctypes.c_void_p(self.stream.cuda_stream), int(track_rho), float(eps0),
+                        float(mu0), float(storage_scale))
+        self.storage = storage
         h = ctypes.c_void_p()
         rc = self.lib.lbm_create(MODELS[model], nx, ny, nz, ctypes.byref(media), ctypes.byref(opts), ctypes.byref(h))
         if rc != 0:
@@ -264,9 +269,11 @@ class Lattice:
         return True
 
 
-def lattice_from_workload(w, *, track_rho: bool = False, stream=None, init: bool = True) -> Lattice:
+def lattice_from_workload(w, *, track_rho: bool = False, stream=None, init: bool = True, storage: str = "f32",
+                          storage_scale: float = 0.0) -> Lattice:
     """Build a Lattice from a ``workloads.Workload``: media, sources and initial fields."""
-    L = Lattice(w.model, w.shape, w.eps_r, w.mu_r, w.sigma, track_rho=track_rho, stream=stream)
+    L = Lattice(w.model, w.shape, w.eps_r, w.mu_r, w.sigma, track_rho=track_rho, stream=stream, storage=storage,
+                storage_scale=storage_scale)
     for s in w.sources:
         L.add_source(s)
     if init:

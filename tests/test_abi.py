@@ -41,10 +41,13 @@ def test_create_rejects_bad_arguments_without_touching_a_gpu(lib):
     assert b"unknown model" in lib.lbm_last_error(None)
     assert lib.lbm_create(0, 0, 4, 4, None, None, ctypes.byref(h)) == -1
     assert lib.lbm_create(0, 65536, 65536, 2, None, None, ctypes.byref(h)) == -1
-    opts = lbm._Options(0, None, 0, 1.0, 9.0)
+    opts = lbm._Options(0, None, 0, 1.0, 9.0, 0.0)
     assert lib.lbm_create(0, 4, 4, 4, None, ctypes.byref(opts), ctypes.byref(h)) == -6  # MM fixes eps0, mu0
-    opts = lbm._Options(1, None, 0, 0.0, 0.0)
-    assert lib.lbm_create(1, 4, 4, 4, None, ctypes.byref(opts), ctypes.byref(h)) == -6  # BF16 not built
+    opts = lbm._Options(7, None, 0, 0.0, 0.0, 0.0)
+    assert lib.lbm_create(1, 4, 4, 4, None, ctypes.byref(opts), ctypes.byref(h)) == -1  # unknown storage
+    opts = lbm._Options(2, None, 0, 0.0, 0.0, 3.0)
+    assert lib.lbm_create(1, 4, 4, 4, None, ctypes.byref(opts), ctypes.byref(h)) == -1  # scale not a power of 2
+    assert b"power of two" in lib.lbm_last_error(None)
     assert lib.lbm_create(0, 4, 4, 4, None, None, None) == -1
     assert not h.value
 

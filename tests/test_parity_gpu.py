@@ -267,3 +267,25 @@ def test_bad_arguments_are_reported():
         L.add_source(bad)
     with pytest.raises(LbmError, match="EINVAL"):
         L.step(-1)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("media", ["few", "random"])
+def test_field_quotients_are_correctly_rounded(model, media):
+    """The kernels divide without a divide instruction (x r corrected by one fused multiply-add,
+    with r = RN(1/d)). The fields they report must equal IEEE division of the reported D and B,
+    bit for bit: E = D / (eps0 eps_r) and H = B / (mu0 mu_r)."""
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    w, f = wl.random_state(model, (17, 9, 6), seed=41, media=media, n_sources=0)
+    w = rounded(w)
+    L = lattice_from_workload(w, init=False)
+    L.set_populations(np.asarray(f, np.float32) * 1e-3, 0)
+    L.step(2)
+    F = L.fields("EBDH")
+    eps0, mu0 = (1.0, 2.0) if model == "mm" else (3.0, 3.0)
+    er = torch.tensor(np.ones(w.n) if w.eps_r is None else w.eps_r, dtype=torch.float32, device="cuda")
+    mr = torch.tensor(np.ones(w.n) if w.mu_r is None else w.mu_r, dtype=torch.float32, device="cuda")
+    eps = er * eps0  # exact: eps0 is 1 or 3
+    mu = mr * mu0
+    assert torch.equal(F["E"], F["D"] / eps)
+    assert torch.equal(F["H"], F["B"] / mu)
