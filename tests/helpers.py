@@ -53,3 +53,22 @@ def peak_interp(y):
         return float(y0)
     off = 0.5 * (ym - yp) / den
     return float(y0 - 0.25 * (ym - yp) * off)
+
+
+def fresnel_interface_errors(run, model, lz):
+    """Section IV-A on a 1 x 1 x Lz lattice: Gaussian pulse (eq. Initialpulse) at z0 = Lz/2 - Lz/6
+    with alpha = 0.05 Lz / sqrt(2), eps_r = 2.5 for z >= Lz/2. Returns the relative errors of the
+    reflected and transmitted peak amplitudes against Fresnel, measured 0.3 Lz / C after the pulse
+    reaches the interface. ``run(eps_r, E, B, steps)`` returns E_x after that many steps."""
+    from paper_2309_08068_gb300 import workloads as wl
+    c = wl.LIGHT_SPEED[model]
+    z = np.arange(lz, dtype=np.float64)
+    eps = np.where(z >= lz / 2, 2.5, 1.0)
+    alpha = 0.05 * lz / np.sqrt(2.0)
+    E, B = wl.gaussian_pulse_fields(model, z, lz / 2 - lz / 6, alpha, 1.0)
+    ex = np.asarray(run(eps, E, B, int(round((lz / 6) / c + 0.3 * lz / c))), dtype=np.float64)
+    r = np.sqrt(2.5)
+    R, T = -(r - 1) / (r + 1), 2 / (r + 1)
+    a_r = peak_interp(ex[: lz // 2 - int(2 * alpha)])
+    a_t = peak_interp(ex[lz // 2 + int(alpha):])
+    return abs(a_r - R) / abs(R), abs(a_t - T) / T

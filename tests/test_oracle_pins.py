@@ -13,7 +13,7 @@ import os
 import numpy as np
 import pytest
 
-from helpers import operator_matrix, oracle_from_workload, peak_interp
+from helpers import fresnel_interface_errors, operator_matrix, oracle_from_workload, peak_interp
 from oracle import OracleLattice, TimeFn
 from paper_2309_08068_gb300 import workloads as wl
 
@@ -413,3 +413,18 @@ def test_current_sheet_radiates_half_impedance(model):
     z_expected = np.sqrt(mu0 / eps0) / 2.0
     for side in (amp[zs + 20: zs + reach - 40], amp[zs - reach + 40: zs - 20]):
         assert np.all(np.abs(side / z_expected - 1.0) < 0.02)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_reflection_error_falls_as_a_power_law(model):
+    """Section IV-A: the amplitude error decreases following a power law as the grid is refined.
+    With a sharp eps_r step the reflected amplitude converges at first order (slope 1 within 0.3 over
+    each doubling, Lz = 256 ... 2048); the transmitted error is erratic, as the paper also notes."""
+    def run(eps, E, B, steps):
+        L = OracleLattice(model, (1, 1, eps.size), eps_r=eps, threads=8)
+        L.init_fields(E, B)
+        L.step(steps)
+        return L.fields()["E"][0]
+    errs = [fresnel_interface_errors(run, model, lz)[0] for lz in (256, 512, 1024, 2048)]
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(slopes - 1.0) < 0.35), slopes
