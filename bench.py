@@ -208,6 +208,52 @@ def storage_accuracy(storages=("f32", "bf16", "f16")):
     return out
 
 
+def refinement_sweep(stream, steps: int):
+    """The skin-effect mesh-refinement sweep (16 lattices N = 32 ... 272, 95.9 M cells, sigma = 0.1):
+    `steps` steps of every lattice, batched (one launch per step, captured graph, autotuned launch
+    configuration) against each lattice stepped on its own, same stream, same data."""
+    import torch
+    from paper_2309_08068_gb300.lbm import Batch, lattice_from_workload
+    out = {}
+    for model in ("mm", "hv"):
+        works = wl.refinement_batch(model, 0.1)
+        cells = sum(w.n for w in works)
+        with torch.cuda.stream(stream):
+            lats = [lattice_from_workload(w, stream=stream) for w in works]
+        batch = Batch(lats)
+        block, persistent = batch.autotune(3)
+        batch.step(2)  # capture the graph of a 2-step call, then time fresh calls
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_capture = e0.elapsed_time(e1)
+        e0.record(stream)
+        batch.step(steps)  # same call again: graph replay
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batched = e0.elapsed_time(e1)
+        e0.record(stream)
+        for _ in range(steps):
+            for L in lats:
+                L.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_single = e0.elapsed_time(e1)
+        out[model] = {"lattices": len(works), "cells": cells, "steps": steps,
+                      "batched_graph_MLUPS": round(cells * steps / (ms_batched * 1e-3) / 1e6, 1),
+                      "per_lattice_launches_MLUPS": round(cells * steps / (ms_single * 1e-3) / 1e6, 1),
+                      "first_call_with_capture_ms": round(ms_capture, 2),
+                      "autotuned": {"block": block, "persistent": persistent}}
+        batch.close()
+        for L in lats:
+            L.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -325,6 +371,7 @@ def run_ours(args):
                                    "steps_timed": kv}
             Lv.close()
     accuracy = storage_accuracy() if rank == 0 else None
+    refinement = refinement_sweep(stream, args.refine_steps) if args.refine_steps > 0 else None
 
     # end to end through the C ABI with host buffers: upload fields, K steps, read E and B back
     pinned_E = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
@@ -392,6 +439,7 @@ def run_ours(args):
             st: {m: dict(v, frac=round(v["algorithmic_GBps"] / peak, 4)) for m, v in variants[st].items()}
             for st in variants},
         "rel_l2_vs_fp64_dielectric_pulse_1500": accuracy,
+        "refinement_batch": refinement,
         "gpu_launches": int(launches),
         "finite": finite,
         "clocks": clocks.summary(),
@@ -410,6 +458,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--refine-steps", type=int, default=100,
+                    help="steps of the batched refinement-sweep measurement (0 skips it)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="population storage of the main timed run (arithmetic is FP32 in every case)")
     args = ap.parse_args()

@@ -198,6 +198,45 @@ int lbm_sync(lbm_ctx* ctx);
 /* Free the context and its device memory. NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched stepping of lattices of uneven sizes. The paper's studies are mesh-refinement sweeps:
+ * the same test on lattices refined step by step (Section IV, "for different refinements of the
+ * grid"). A batch advances all of them together, one fused launch per time step over every active
+ * lattice, and replays the whole sequence as one captured CUDA graph. A small lattice alone cannot
+ * fill the GPU, so batching is what keeps it busy.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* Group count >= 1 distinct contexts of the same model, storage, track_rho, CUDA stream and device.
+ * The batch keeps the pointers: the contexts stay owned by the caller and must outlive the batch.
+ * Sources and populations may still be changed between calls through the context API. */
+int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out);
+
+/* Advance context k by steps[k] >= 0 time steps (results identical, bit for bit, to lbm_step on each
+ * context). Step j of the call updates every context with steps[k] > j in one launch (plus one launch
+ * for source cells); each context's time and sources advance as in lbm_step. On a non-default stream the
+ * whole call is captured once into a CUDA graph and replayed by later calls with the same steps,
+ * sizes and source-cell counts; on the legacy default stream the launches are issued directly.
+ * Asynchronous: enqueued on the contexts' stream. */
+int lbm_batch_step(lbm_batch* b, const int* steps);
+
+/* Time trial_steps launches of each launch configuration (128 or 256 threads per block; one block
+ * per tile, or a persistent grid of resident blocks striding over the tiles) on this batch and keep
+ * the fastest. The trial launches rewrite only the spare population buffers, so the lattices' state
+ * is unchanged. Waits for the stream. The chosen configuration is returned when the pointers are
+ * non-NULL. */
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* block_out, int* persistent_out);
+
+/* Set the launch configuration directly: block is 128 or 256, persistent 0 or 1. */
+int lbm_batch_set_config(lbm_batch* b, int block, int persistent);
+
+/* Kernel launches enqueued by the batch so far (graph replays count their kernels). */
+int64_t lbm_batch_launch_count(const lbm_batch* b);
+/* Message of the last failing batch call (or of the last failing lbm_batch_create when b is NULL). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+/* Free the batch (not its contexts). NULL is accepted. */
+int lbm_batch_destroy(lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -822,3 +822,361 @@ extern "C" int lbm_reduce_noalloc(lbm_ctx* ctx, double* out, int on_device) {
     }
     return LBM_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Batched stepping of several lattices (mesh-refinement sweeps): lbm_batch_*.
+// ------------------------------------------------------------------------------------------------
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctx;
+    int model = 0, storage = 0, device = 0;
+    bool rho = false;
+    cudaStream_t stream = nullptr;
+    int block = 256;     // threads per block of the main launch
+    int persistent = 0;  // 1: grid of resident blocks striding over the tiles
+    BatchLattice* d_lat = nullptr;
+    BatchTile* d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    BatchTile* d_stiles = nullptr;
+    size_t stiles_cap = 0;
+    float* d_stable = nullptr;
+    size_t stable_cap = 0;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> graph_key;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int bfail(lbm_batch* b, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define BCUDA_TRY(b, call)                                                                          \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return bfail((b), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void drop_graph(lbm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_key.clear();
+}
+
+template <class T>
+int ensure_capacity(lbm_batch* b, T** p, size_t* cap, size_t count) {
+    if (count <= *cap) return LBM_OK;
+    drop_graph(b);  // a captured graph holds the old address
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LBM_ENOMEM, "batch: cannot allocate %zu entries", count);
+    }
+    *cap = count;
+    return LBM_OK;
+}
+
+// Lattice order (decreasing step count, so the active lattices of any step form a prefix), tiles and
+// per-step active tile counts for the current block size.
+struct BatchPlan {
+    std::vector<int> order;
+    std::vector<BatchTile> tiles, stiles;
+    std::vector<int> tile_end, stile_end;  // cumulative counts per lattice in order
+    int max_steps = 0;
+};
+
+BatchPlan plan_batch(const lbm_batch* b, const int* steps) {
+    BatchPlan p;
+    const int count = (int)b->ctx.size();
+    p.order.resize(count);
+    for (int k = 0; k < count; ++k) p.order[k] = k;
+    std::stable_sort(p.order.begin(), p.order.end(), [&](int x, int y) { return steps[x] > steps[y]; });
+    for (int k : p.order) {
+        const lbm_ctx* c = b->ctx[k];
+        for (int begin = 0; begin < c->g.n; begin += b->block) p.tiles.push_back(BatchTile{k, begin});
+        for (int begin = 0; begin < c->n_special; begin += kBlock) p.stiles.push_back(BatchTile{k, begin});
+        p.tile_end.push_back((int)p.tiles.size());
+        p.stile_end.push_back((int)p.stiles.size());
+        p.max_steps = std::max(p.max_steps, steps[k]);
+    }
+    return p;
+}
+
+// Number of tiles of the lattices still active at step j (a prefix of the order).
+int active_prefix(const BatchPlan& p, const int* steps, int j, const std::vector<int>& ends) {
+    int last = -1;
+    for (size_t r = 0; r < p.order.size(); ++r)
+        if (steps[p.order[r]] > j) last = (int)r;
+    return last < 0 ? 0 : ends[(size_t)last];
+}
+
+// Upload descriptors (and source tables) for a call advancing lattice k by steps[k].
+int upload_batch(lbm_batch* b, const int* steps, int max_steps) {
+    const int count = (int)b->ctx.size();
+    size_t stable_size = 0;
+    for (int k = 0; k < count; ++k) stable_size += b->ctx[k]->sources.size() * (size_t)std::max(max_steps, 1);
+    int rc;
+    if ((rc = ensure_capacity(b, &b->d_stable, &b->stable_cap, std::max<size_t>(stable_size, 1))) != LBM_OK) return rc;
+    std::vector<float> table(std::max<size_t>(stable_size, 1), 0.f);
+    std::vector<BatchLattice> lat((size_t)count);
+    size_t off = 0;
+    for (int k = 0; k < count; ++k) {
+        lbm_ctx* c = b->ctx[k];
+        BatchLattice& L = lat[(size_t)k];
+        memset(&L, 0, sizeof(L));
+        L.base = base_args(c);
+        for (int q = 0; q < 2; ++q) {
+            L.buf[q] = c->buf[q];
+            L.buf2[q] = c->model == LBM_HV ? c->buf2[q] : c->rest1;
+            L.rho[q] = c->rho[q];
+        }
+        L.cur0 = c->cur;
+        L.steps = steps[k];
+        L.n_src = (int)c->sources.size();
+        L.s_stride = std::max(max_steps, 1);
+        L.s_table = b->d_stable + off;
+        for (int s = 0; s < L.n_src; ++s)
+            for (int j = 0; j < steps[k]; ++j)
+                table[off + (size_t)s * L.s_stride + (size_t)j] = (float)time_value(c->sources[(size_t)s], c->t + 1 + j);
+        off += (size_t)L.n_src * L.s_stride;
+    }
+    BCUDA_TRY(b, cudaMemcpyAsync(b->d_lat, lat.data(), sizeof(BatchLattice) * count, cudaMemcpyHostToDevice, b->stream));
+    BCUDA_TRY(b, cudaMemcpyAsync(b->d_stable, table.data(), sizeof(float) * table.size(), cudaMemcpyHostToDevice,
+                                 b->stream));
+    return LBM_OK;
+}
+
+int upload_tiles(lbm_batch* b, const BatchPlan& p) {
+    int rc;
+    if ((rc = ensure_capacity(b, &b->d_tiles, &b->tiles_cap, std::max<size_t>(p.tiles.size(), 1))) != LBM_OK) return rc;
+    if ((rc = ensure_capacity(b, &b->d_stiles, &b->stiles_cap, std::max<size_t>(p.stiles.size(), 1))) != LBM_OK) return rc;
+    if (!p.tiles.empty())
+        BCUDA_TRY(b, cudaMemcpyAsync(b->d_tiles, p.tiles.data(), sizeof(BatchTile) * p.tiles.size(),
+                                     cudaMemcpyHostToDevice, b->stream));
+    if (!p.stiles.empty())
+        BCUDA_TRY(b, cudaMemcpyAsync(b->d_stiles, p.stiles.data(), sizeof(BatchTile) * p.stiles.size(),
+                                     cudaMemcpyHostToDevice, b->stream));
+    return LBM_OK;
+}
+
+BatchLaunch launch_config(const lbm_batch* b) {
+    BatchLaunch L;
+    L.lat = b->d_lat;
+    L.tiles = b->d_tiles;
+    L.stiles = b->d_stiles;
+    L.block = b->block;
+    L.storage = b->storage;
+    L.rho = b->rho;
+    L.grid_cap = 0;
+    if (b->persistent) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        const int occ = b->model == LBM_MM ? mm_batch_occupancy(b->storage, b->block, b->rho)
+                                           : hv_batch_occupancy(b->storage, b->block);
+        L.grid_cap = std::max(1, sms * std::max(occ, 1));
+    }
+    return L;
+}
+
+// Enqueue every step of the call on the batch stream.
+int enqueue_steps(lbm_batch* b, const BatchPlan& p, const int* steps, int64_t* launched) {
+    const BatchLaunch L = launch_config(b);
+    for (int j = 0; j < p.max_steps; ++j) {
+        const int nt = active_prefix(p, steps, j, p.tile_end);
+        const int ns = active_prefix(p, steps, j, p.stile_end);
+        *launched += b->model == LBM_MM ? mm_launch_batch_step(L, j, nt, ns, b->stream)
+                                        : hv_launch_batch_step(L, j, nt, ns, b->stream);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "batched launch: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: out is NULL");
+    *out = nullptr;
+    if (!ctxs || count < 1) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: need at least one context");
+    for (int k = 0; k < count; ++k) {
+        if (!ctxs[k]) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d is NULL", k);
+        for (int q = 0; q < k; ++q)
+            if (ctxs[q] == ctxs[k]) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d repeated", k);
+        if (ctxs[k]->model != ctxs[0]->model || ctxs[k]->storage != ctxs[0]->storage ||
+            ctxs[k]->stream != ctxs[0]->stream || ctxs[k]->device != ctxs[0]->device ||
+            (ctxs[k]->rho[0] != nullptr) != (ctxs[0]->rho[0] != nullptr))
+            return bfail(nullptr, LBM_EINVAL,
+                         "lbm_batch_create: contexts must share model, storage, track_rho, stream and device");
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: out of host memory");
+    b->ctx.assign(ctxs, ctxs + count);
+    b->model = ctxs[0]->model;
+    b->storage = ctxs[0]->storage;
+    b->device = ctxs[0]->device;
+    b->rho = ctxs[0]->rho[0] != nullptr;
+    b->stream = ctxs[0]->stream;
+    if (cudaMalloc(&b->d_lat, sizeof(BatchLattice) * count) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return bfail(nullptr, LBM_ENOMEM, "lbm_batch_create: cannot allocate descriptors");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_config(lbm_batch* b, int block, int persistent) {
+    if (!b) return LBM_EINVAL;
+    if (block != 128 && block != 256) return bfail(b, LBM_EINVAL, "lbm_batch_set_config: block must be 128 or 256");
+    if (block != b->block || (persistent != 0) != (b->persistent != 0)) drop_graph(b);
+    b->block = block;
+    b->persistent = persistent != 0;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, const int* steps) {
+    if (!b) return LBM_EINVAL;
+    if (!steps) return bfail(b, LBM_EINVAL, "lbm_batch_step: steps is NULL");
+    const int count = (int)b->ctx.size();
+    for (int k = 0; k < count; ++k)
+        if (steps[k] < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: steps[%d] < 0", k);
+    int dev = -1;
+    BCUDA_TRY(b, cudaGetDevice(&dev));
+    if (dev != b->device) BCUDA_TRY(b, cudaSetDevice(b->device));
+    const BatchPlan p = plan_batch(b, steps);
+    if (p.max_steps == 0) return LBM_OK;
+    int rc;
+    if ((rc = upload_tiles(b, p)) != LBM_OK) return rc;
+    if ((rc = upload_batch(b, steps, p.max_steps)) != LBM_OK) return rc;
+    // The sequence of launches depends only on the steps, the lattice sizes and the configuration;
+    // everything else is read from the descriptors, so a captured graph replays for later calls.
+    std::vector<long long> key{b->block, b->persistent};
+    for (int k = 0; k < count; ++k) {
+        key.push_back(steps[k]);
+        key.push_back(b->ctx[k]->g.n);
+        key.push_back(b->ctx[k]->n_special);
+        key.push_back((long long)b->ctx[k]->sources.size());
+    }
+    int64_t launched = 0;
+    if (b->stream == nullptr) {
+        // The legacy default stream cannot be captured: launch directly.
+        if ((rc = enqueue_steps(b, p, steps, &launched)) != LBM_OK) return rc;
+    } else {
+        if (!b->exec || key != b->graph_key) {
+            drop_graph(b);
+            cudaGraph_t graph = nullptr;
+            BCUDA_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue_steps(b, p, steps, &launched);
+            cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+            if (rc != LBM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                b->exec = nullptr;
+                return bfail(b, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            }
+            b->graph_key = key;
+        } else {
+            for (int j = 0; j < p.max_steps; ++j)
+                launched += (active_prefix(p, steps, j, p.tile_end) > 0) + (active_prefix(p, steps, j, p.stile_end) > 0);
+        }
+        BCUDA_TRY(b, cudaGraphLaunch(b->exec, b->stream));
+    }
+    b->launches += launched;
+    for (int k = 0; k < count; ++k) {
+        lbm_ctx* c = b->ctx[k];
+        c->cur = (c->cur + steps[k]) & 1;
+        c->t += steps[k];
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* block_out, int* persistent_out) {
+    if (!b) return LBM_EINVAL;
+    if (trial_steps < 1) return bfail(b, LBM_EINVAL, "lbm_batch_autotune: trial_steps must be >= 1");
+    const int count = (int)b->ctx.size();
+    std::vector<int> ones((size_t)count, 1);
+    cudaEvent_t e0, e1;
+    BCUDA_TRY(b, cudaEventCreate(&e0));
+    BCUDA_TRY(b, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_block = b->block, best_persistent = b->persistent;
+    const int blocks[2] = {128, 256};
+    int rc = LBM_OK;
+    for (int bi = 0; bi < 2 && rc == LBM_OK; ++bi) {
+        for (int pers = 0; pers < 2 && rc == LBM_OK; ++pers) {
+            b->block = blocks[bi];
+            b->persistent = pers;
+            const BatchPlan p = plan_batch(b, ones.data());
+            if ((rc = upload_tiles(b, p)) != LBM_OK) break;
+            if ((rc = upload_batch(b, ones.data(), 1)) != LBM_OK) break;
+            const BatchLaunch L = launch_config(b);
+            const int nt = (int)p.tiles.size();
+            // Step j = 0 repeatedly: reads the current buffers and rewrites the spare ones, so the
+            // lattices' state is unchanged.
+            auto run = [&]() {
+                return b->model == LBM_MM ? mm_launch_batch_step(L, 0, nt, 0, b->stream)
+                                          : hv_launch_batch_step(L, 0, nt, 0, b->stream);
+            };
+            run();
+            cudaEventRecord(e0, b->stream);
+            for (int s = 0; s < trial_steps; ++s) b->launches += run();
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+                rc = bfail(b, LBM_ECUDA, "lbm_batch_autotune: trial launch failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_block = blocks[bi];
+                best_persistent = pers;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    drop_graph(b);
+    b->block = best_block;
+    b->persistent = best_persistent;
+    if (rc != LBM_OK) return rc;
+    if (block_out) *block_out = best_block;
+    if (persistent_out) *persistent_out = best_persistent;
+    return LBM_OK;
+}
+
+int64_t lbm_batch_launch_count(const lbm_batch* b) { return b ? b->launches : -1; }
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(b);
+    if (b->d_lat) cudaFree(b->d_lat);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_stiles) cudaFree(b->d_stiles);
+    if (b->d_stable) cudaFree(b->d_stable);
+    delete b;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -94,7 +94,8 @@ __device__ __forceinline__ HVFields hv_fields(const float4 (&e)[6], const float2
     F.B = make_float3(bx, by, bz);
     F.E = make_float3(div_rn(dx, eps, inv_eps), div_rn(dy, eps, inv_eps), div_rn(dz, eps, inv_eps));
     F.H = make_float3(div_rn(bx, mu, inv_mu), div_rn(by, mu, inv_mu), div_rn(bz, mu, inv_mu));
-    F.J = make_float3(sigma * F.E.x + jext.x, sigma * F.E.y + jext.y, sigma * F.E.z + jext.z);
+    F.J = make_float3(__fmaf_rn(sigma, F.E.x, jext.x), __fmaf_rn(sigma, F.E.y, jext.y),
+                      __fmaf_rn(sigma, F.E.z, jext.z));
     return F;
 }
 
@@ -115,17 +116,9 @@ __device__ __forceinline__ float3 hv_h(float3 B, const MatCoef& mat) {
     return make_float3(div_rn(B.x, mu, inv_mu), div_rn(B.y, mu, inv_mu), div_rn(B.z, mu, inv_mu));
 }
 
+// Update of cell i; m is its index in the special-cell list when kSpecial.
 template <int S, int M, bool kSpecial>
-__global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
-    int i, m = 0;
-    if constexpr (kSpecial) {
-        m = blockIdx.x * blockDim.x + threadIdx.x;
-        if (m >= a.sv.n_special) return;
-        i = a.sv.cell[m];
-    } else {
-        i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.g.n) return;
-    }
+__device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m) {
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 e[6];
     float2 hy[6];
@@ -164,6 +157,19 @@ __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
         }
         hv_put<S>(a, k, i, make_float4(eo.x, eo.y, eo.z, ho.x), make_float2(ho.y, ho.z));
     });
+}
+
+template <int S, int M, bool kSpecial>
+__global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
+    if constexpr (kSpecial) {
+        const int m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        hv_update<S, M, kSpecial>(a, a.sv.cell[m], m);
+    } else {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+        hv_update<S, M, kSpecial>(a, i, 0);
+    }
 }
 
 // Equilibria for fields E, B and J = 0 (Appendix B initialisation), stored so that cell x pulls
@@ -288,6 +294,41 @@ __global__ void __launch_bounds__(kBlock) hv_reduce_kernel(StepArgs a, double* _
     block_sum3_store(w, f2, 0.0, partials + 3 * blockIdx.x);
 }
 
+// Batched step j of several lattices (see mm_batch_kernel).
+template <int S, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) hv_batch_kernel(const BatchLattice* __restrict__ lat,
+                                                         const BatchTile* __restrict__ tiles, int n_tiles, int j) {
+    for (int b = blockIdx.x; b < n_tiles; b += gridDim.x) {
+        const BatchTile tile = tiles[b];
+        const BatchLattice* L = &lat[tile.lattice];
+        const int i = tile.begin + threadIdx.x;
+        if (j >= L->steps || i >= L->base.g.n) continue;
+        const StepArgs a = batch_args(L, j);
+        switch (a.media_mode) {
+            case kUniform: hv_update<S, kUniform, false>(a, i, 0); break;
+            case kTable: hv_update<S, kTable, false>(a, i, 0); break;
+            default: hv_update<S, kPerCell, false>(a, i, 0); break;
+        }
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kBlock) hv_batch_special_kernel(const BatchLattice* __restrict__ lat,
+                                                                  const BatchTile* __restrict__ tiles, int j) {
+    const BatchTile tile = tiles[blockIdx.x];
+    const BatchLattice* L = &lat[tile.lattice];
+    const int m = tile.begin + threadIdx.x;
+    if (j >= L->steps || m >= L->base.sv.n_special) return;
+    StepArgs a = batch_args(L, j);
+    batch_sources(L, j, a);
+    const int i = a.sv.cell[m];
+    switch (a.media_mode) {
+        case kUniform: hv_update<S, kUniform, true>(a, i, m); break;
+        case kTable: hv_update<S, kTable, true>(a, i, m); break;
+        default: hv_update<S, kPerCell, true>(a, i, m); break;
+    }
+}
+
 }  // namespace
 
 int hv_launch_step(const StepArgs& a, cudaStream_t st) {
@@ -356,6 +397,34 @@ int hv_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* 
         });
     });
     return 1 + launch_reduce_partials(partials, n_blocks, result, st);
+}
+
+int hv_launch_batch_step(const BatchLaunch& b, int j, int n_tiles, int n_stiles, cudaStream_t st) {
+    int launched = 0;
+    with_storage(b.storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        if (n_tiles > 0) {
+            const int grid = b.grid_cap > 0 ? (n_tiles < b.grid_cap ? n_tiles : b.grid_cap) : n_tiles;
+            if (b.block == 128) hv_batch_kernel<S, 128><<<grid, 128, 0, st>>>(b.lat, b.tiles, n_tiles, j);
+            else hv_batch_kernel<S, 256><<<grid, 256, 0, st>>>(b.lat, b.tiles, n_tiles, j);
+            ++launched;
+        }
+        if (n_stiles > 0) {
+            hv_batch_special_kernel<S><<<n_stiles, kBlock, 0, st>>>(b.lat, b.stiles, j);
+            ++launched;
+        }
+    });
+    return launched;
+}
+
+int hv_batch_occupancy(int storage, int block) {
+    int blocks = 0;
+    with_storage(storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        if (block == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, hv_batch_kernel<S, 128>, 128, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, hv_batch_kernel<S, 256>, 256, 0);
+    });
+    return blocks;
 }
 
 }  // namespace lbm

@@ -362,6 +362,71 @@ __device__ __forceinline__ void block_sum3_store(double a0, double a1, double a2
     }
 }
 
+// --- batched stepping of several lattices -------------------------------------------------
+// One lattice of a batch as the batched kernels read it from device memory. The host rewrites the
+// array before every batched call, so a captured graph of the call replays on fresh contents.
+struct BatchLattice {
+    StepArgs base;         // geometry, media, special cells, imposed vectors, storage, eps0, mu0
+    void* buf[2];          // population buffers; step j reads buf[(cur0 + j) & 1]
+    void* buf2[2];         // HV second arrays (MM: unused)
+    float* rho[2];         // MM rest population f_0^(0) when tracked, else null
+    const float* s_table;  // source values s_k(t0 + j + 1) at [k * s_stride + j]
+    int s_stride;
+    int n_src;
+    int cur0;   // buffer index holding the state when the call starts
+    int steps;  // steps this lattice advances in the call
+};
+
+// A block's share of the batch: cells [begin, begin + blockDim) of one lattice (or, for the
+// source-cell launch, special cells [begin, begin + blockDim)).
+struct BatchTile {
+    int lattice;
+    int begin;
+};
+
+// StepArgs of lattice L at batch step j (buffers and storage; sources are filled by the caller).
+__device__ __forceinline__ StepArgs batch_args(const BatchLattice* __restrict__ L, int j) {
+    StepArgs a;
+    a.g = L->base.g;
+    a.media_mode = L->base.media_mode;
+    a.media = L->base.media;
+    const int in = (L->cur0 + j) & 1, out = in ^ 1;
+    a.fin = L->buf[in];
+    a.fout = L->buf[out];
+    a.fin2 = L->buf2[in];
+    a.fout2 = L->buf2[out];
+    a.rho_in = L->rho[in];
+    a.rho_out = L->rho[out];
+    a.eps0 = L->base.eps0;
+    a.mu0 = L->base.mu0;
+    a.storage = L->base.storage;
+    a.scale = L->base.scale;
+    a.inv_scale = L->base.inv_scale;
+    a.sv = L->base.sv;
+    return a;
+}
+
+// Source values of lattice L at batch step j, and its imposed-field vectors.
+__device__ __forceinline__ void batch_sources(const BatchLattice* __restrict__ L, int j, StepArgs& a) {
+    for (int k = 0; k < L->n_src; ++k) {
+        a.sc.s[k] = L->s_table[k * L->s_stride + j];
+        for (int q = 0; q < 3; ++q) {
+            a.sc.E0[k][q] = L->base.sc.E0[k][q];
+            a.sc.B0[k][q] = L->base.sc.B0[k][q];
+        }
+    }
+}
+
+struct BatchLaunch {
+    const BatchLattice* lat;
+    const BatchTile* tiles;   // main tiles, lattices in decreasing step count
+    const BatchTile* stiles;  // special-cell tiles, same lattice order
+    int block;                // threads per block of the main launch (128 or 256)
+    int grid_cap;             // persistent launch: blocks in the grid (0 = one block per tile)
+    int storage;
+    bool rho;
+};
+
 // --- host-side launchers (one set per model) -----------------------------------------------
 // Each returns the number of kernels it enqueued (errors are read with cudaGetLastError).
 int mm_launch_step(const StepArgs& a, cudaStream_t st);
@@ -380,5 +445,13 @@ int hv_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* 
 
 // Deterministic double reduction of per-block partial sums (3 values per block, fixed order).
 int launch_reduce_partials(const double* partials, int n_blocks, double* result, cudaStream_t st);
+
+// Batched step j: main launch over the first n_tiles tiles, source-cell launch over the first
+// n_stiles special tiles. Returns the number of kernels enqueued.
+int mm_launch_batch_step(const BatchLaunch& b, int j, int n_tiles, int n_stiles, cudaStream_t st);
+int hv_launch_batch_step(const BatchLaunch& b, int j, int n_tiles, int n_stiles, cudaStream_t st);
+// Resident blocks per SM of the main batched kernel for this configuration.
+int mm_batch_occupancy(int storage, int block, bool rho);
+int hv_batch_occupancy(int storage, int block);
 
 }  // namespace lbm

@@ -105,9 +105,12 @@ __device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0
     o.E.y = div_rn(o.Dpp.y, er, inv_er);
     o.E.z = div_rn(o.Dpp.z, er, inv_er);
     o.B = make_float3(bx, by, bz);
-    o.J.x = sigma * o.E.x + jext.x;
-    o.J.y = sigma * o.E.y + jext.y;
-    o.J.z = sigma * o.E.z + jext.z;
+    // Explicit fused multiply-adds wherever a product is inexact, so that the result does not
+    // depend on the compiler's contraction choices (the batched and single-lattice kernels inline
+    // this code in different contexts and must agree bit for bit).
+    o.J.x = __fmaf_rn(sigma, o.E.x, jext.x);
+    o.J.y = __fmaf_rn(sigma, o.E.y, jext.y);
+    o.J.z = __fmaf_rn(sigma, o.E.z, jext.z);
     o.rho = rho;
     o.inv4mu = mat.c0.w;
     return o;
@@ -130,17 +133,9 @@ __device__ __forceinline__ void mm_put(const StepArgs& a, int d, int i, float4 v
     fout[(size_t)d * a.g.n + i] = Pack4<S>::pack(v, a.scale);
 }
 
+// Update of cell i; m is its index in the special-cell list when kSpecial.
 template <int S, int M, bool kSpecial, bool kRho>
-__global__ void __launch_bounds__(kBlock, 3) mm_step_kernel(StepArgs a) {
-    int i, m = 0;
-    if constexpr (kSpecial) {
-        m = blockIdx.x * blockDim.x + threadIdx.x;
-        if (m >= a.sv.n_special) return;
-        i = a.sv.cell[m];
-    } else {
-        i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.g.n) return;
-    }
+__device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m) {
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 f[12];
     mm_pull<S>(a, h, f);
@@ -161,7 +156,7 @@ __global__ void __launch_bounds__(kBlock, 3) mm_step_kernel(StepArgs a) {
         constexpr int b0 = kMMB[d][0], b1 = kMMB[d][1], b2 = kMMB[d][2];
         const float two_s = 0.125f * sdot<v0, v1, v2>(F.J.x, F.J.y, F.J.z);
         const float bb = sdot<b0, b1, b2>(F.B.x, F.B.y, F.B.z);
-        const float two_alpha = 0.25f * sdot<e0, e1, e2>(F.Dpp.x, F.Dpp.y, F.Dpp.z) + bb * F.inv4mu;
+        const float two_alpha = __fmaf_rn(bb, F.inv4mu, 0.25f * sdot<e0, e1, e2>(F.Dpp.x, F.Dpp.y, F.Dpp.z));
         const float two_beta = 0.25f * sdot<e0, e1, e2>(F.E.x, F.E.y, F.E.z) + 0.25f * bb;
         float4 o;
         o.x = two_s + two_alpha - f[d].x;
@@ -172,7 +167,7 @@ __global__ void __launch_bounds__(kBlock, 3) mm_step_kernel(StepArgs a) {
             if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
                 const float bi = sdot<b0, b1, b2>(cs.B.x, cs.B.y, cs.B.z);
                 const float ee = sdot<e0, e1, e2>(cs.E.x, cs.E.y, cs.E.z);
-                const float alpha = 0.125f * (mat.c0.x * ee) + 0.5f * bi * F.inv4mu;
+                const float alpha = __fmaf_rn(0.5f * bi, F.inv4mu, 0.125f * __fmul_rn(mat.c0.x, ee));
                 const float beta = 0.125f * ee + 0.125f * bi;
                 o = make_float4(alpha, -alpha, beta, -beta);
             }
@@ -180,6 +175,19 @@ __global__ void __launch_bounds__(kBlock, 3) mm_step_kernel(StepArgs a) {
         mm_put<S>(a, d, i, o);
     });
     if constexpr (kRho) a.rho_out[i] = 2.f * F.rho - rest0;  // f_0^(0)eq = rho_c; stays in place
+}
+
+template <int S, int M, bool kSpecial, bool kRho>
+__global__ void __launch_bounds__(kBlock, 3) mm_step_kernel(StepArgs a) {
+    if constexpr (kSpecial) {
+        const int m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        mm_update<S, M, kSpecial, kRho>(a, a.sv.cell[m], m);
+    } else {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+        mm_update<S, M, kSpecial, kRho>(a, i, 0);
+    }
 }
 
 // Equilibrium populations of cell x for fields E, B and J = 0 (Appendix B initialisation).
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) mm_init_kernel(StepArgs a, const float
         const MatCoef mat = load_coef<kModelMM, M>(a.media, x, a.eps0, a.mu0);
         const float ee = sdot<e0, e1, e2>(__ldg(&E[x]), __ldg(&E[n + x]), __ldg(&E[2 * n + x]));
         const float bb = sdot<b0, b1, b2>(__ldg(&B[x]), __ldg(&B[n + x]), __ldg(&B[2 * n + x]));
-        const float alpha = 0.125f * (mat.c0.x * ee) + bb * (0.5f * mat.c0.w);  // 0.5 / (4 mu_r)
+        const float alpha = __fmaf_rn(bb, 0.5f * mat.c0.w, 0.125f * __fmul_rn(mat.c0.x, ee));  // 0.5 / (4 mu_r)
         const float beta = 0.125f * ee + 0.125f * bb;
         mm_put<S>(a, d, y, make_float4(alpha, -alpha, beta, -beta));
     });
@@ -332,6 +340,43 @@ __global__ void __launch_bounds__(kBlock) mm_reduce_special_kernel(StepArgs a, d
     block_sum3_store(w, 0.0, 0.0, partials + 3 * blockIdx.x);
 }
 
+// Batched step j of several lattices: each block takes tiles (lattice, first cell) in turn; with a
+// grid smaller than the tile count the blocks persist and stride over the tiles.
+template <int S, int BLOCK, bool kRho>
+__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) mm_batch_kernel(const BatchLattice* __restrict__ lat,
+                                                                        const BatchTile* __restrict__ tiles,
+                                                                        int n_tiles, int j) {
+    for (int b = blockIdx.x; b < n_tiles; b += gridDim.x) {
+        const BatchTile tile = tiles[b];
+        const BatchLattice* L = &lat[tile.lattice];
+        const int i = tile.begin + threadIdx.x;
+        if (j >= L->steps || i >= L->base.g.n) continue;
+        const StepArgs a = batch_args(L, j);
+        switch (a.media_mode) {
+            case kUniform: mm_update<S, kUniform, false, kRho>(a, i, 0); break;
+            case kTable: mm_update<S, kTable, false, kRho>(a, i, 0); break;
+            default: mm_update<S, kPerCell, false, kRho>(a, i, 0); break;
+        }
+    }
+}
+
+template <int S, bool kRho>
+__global__ void __launch_bounds__(kBlock) mm_batch_special_kernel(const BatchLattice* __restrict__ lat,
+                                                                  const BatchTile* __restrict__ tiles, int j) {
+    const BatchTile tile = tiles[blockIdx.x];
+    const BatchLattice* L = &lat[tile.lattice];
+    const int m = tile.begin + threadIdx.x;
+    if (j >= L->steps || m >= L->base.sv.n_special) return;
+    StepArgs a = batch_args(L, j);
+    batch_sources(L, j, a);
+    const int i = a.sv.cell[m];
+    switch (a.media_mode) {
+        case kUniform: mm_update<S, kUniform, true, kRho>(a, i, m); break;
+        case kTable: mm_update<S, kTable, true, kRho>(a, i, m); break;
+        default: mm_update<S, kPerCell, true, kRho>(a, i, m); break;
+    }
+}
+
 }  // namespace
 
 int mm_launch_step(const StepArgs& a, cudaStream_t st) {
@@ -415,6 +460,44 @@ int mm_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* 
         });
     });
     return launched + launch_reduce_partials(partials, total, result, st);
+}
+
+int mm_launch_batch_step(const BatchLaunch& b, int j, int n_tiles, int n_stiles, cudaStream_t st) {
+    int launched = 0;
+    with_storage(b.storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        if (n_tiles > 0) {
+            const int grid = b.grid_cap > 0 ? (n_tiles < b.grid_cap ? n_tiles : b.grid_cap) : n_tiles;
+            if (b.block == 128) {
+                if (b.rho) mm_batch_kernel<S, 128, true><<<grid, 128, 0, st>>>(b.lat, b.tiles, n_tiles, j);
+                else mm_batch_kernel<S, 128, false><<<grid, 128, 0, st>>>(b.lat, b.tiles, n_tiles, j);
+            } else {
+                if (b.rho) mm_batch_kernel<S, 256, true><<<grid, 256, 0, st>>>(b.lat, b.tiles, n_tiles, j);
+                else mm_batch_kernel<S, 256, false><<<grid, 256, 0, st>>>(b.lat, b.tiles, n_tiles, j);
+            }
+            ++launched;
+        }
+        if (n_stiles > 0) {
+            if (b.rho) mm_batch_special_kernel<S, true><<<n_stiles, kBlock, 0, st>>>(b.lat, b.stiles, j);
+            else mm_batch_special_kernel<S, false><<<n_stiles, kBlock, 0, st>>>(b.lat, b.stiles, j);
+            ++launched;
+        }
+    });
+    return launched;
+}
+
+int mm_batch_occupancy(int storage, int block, bool rho) {
+    int blocks = 0;
+    with_storage(storage, [&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        if (block == 128)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &blocks, rho ? mm_batch_kernel<S, 128, true> : mm_batch_kernel<S, 128, false>, 128, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &blocks, rho ? mm_batch_kernel<S, 256, true> : mm_batch_kernel<S, 256, false>, 256, 0);
+    });
+    return blocks;
 }
 
 }  // namespace lbm

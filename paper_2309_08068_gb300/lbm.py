@@ -91,6 +91,13 @@ def load_library(path: str | None = None):
         "lbm_last_error": (ctypes.c_char_p, [P]),
         "lbm_sync": (I, [P]),
         "lbm_destroy": (I, [P]),
+        "lbm_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
+        "lbm_batch_step": (I, [P, ctypes.POINTER(I)]),
+        "lbm_batch_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "lbm_batch_set_config": (I, [P, I, I]),
+        "lbm_batch_launch_count": (I64, [P]),
+        "lbm_batch_last_error": (ctypes.c_char_p, [P]),
+        "lbm_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -281,3 +288,52 @@ def lattice_from_workload(w, *, track_rho: bool = False, stream=None, init: bool
         B = np.zeros((3, w.n), np.float32) if w.B is None else w.B
         L.init_fields(E, B)
     return L
+
+
+class Batch:
+    """Several lattices of one model and storage on one stream, stepped together (lbm_batch_*)."""
+
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        self.lib = load_library()
+        arr = (ctypes.c_void_p * len(self.lattices))(*[L.h.value for L in self.lattices])
+        h = ctypes.c_void_p()
+        rc = self.lib.lbm_batch_create(arr, len(self.lattices), ctypes.byref(h))
+        if rc != 0:
+            raise LbmError(rc, self.lib.lbm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LbmError(rc, self.lib.lbm_batch_last_error(self.h).decode())
+
+    def step(self, steps):
+        """Advance lattice k by steps[k] (an int applies to every lattice)."""
+        if isinstance(steps, int):
+            steps = [steps] * len(self.lattices)
+        arr = (ctypes.c_int * len(self.lattices))(*[int(s) for s in steps])
+        self._check(self.lib.lbm_batch_step(self.h, arr))
+
+    def autotune(self, trial_steps: int = 5):
+        block, persistent = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.lbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(block), ctypes.byref(persistent)))
+        return block.value, bool(persistent.value)
+
+    def set_config(self, block: int, persistent: bool):
+        self._check(self.lib.lbm_batch_set_config(self.h, int(block), int(persistent)))
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.lbm_batch_launch_count(self.h))
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            self.lib.lbm_batch_destroy(h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

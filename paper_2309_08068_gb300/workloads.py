@@ -10,6 +10,8 @@ the FP64 oracle can both take their inputs from it. The setups restate the paper
 * ``slab_pulse``           - plane pulse through 64 random dielectric slabs (many interfaces, 3-D).
 * ``multi_interface_1d``   - Section IV-D, pulse through permittivities 1, 1.3, 2, 3.
 * ``skin_effect_1d``       - Section IV-B, plane wave imposed at z = 0 into a conductor.
+* ``skin_effect_3d``, ``refinement_batch`` - the same on N^3 lattices, N = 32 ... 272 (the
+  mesh-refinement sweep run as one batch).
 * ``random_medium_dipole`` - dipole in a per-cell random permittivity.
 * ``random_state``         - random populations and media for element-wise parity tests.
 
@@ -176,6 +178,29 @@ def skin_effect_1d(model: str, nz: int, sigma: float, periods: float = 12.0, e0:
     src = Source("impose", np.array([0], dtype=np.int64), TimeFunction("sin", 1.0, period, 0.0),
                  E0=(e0, 0.0, 0.0), B0=(0.0, e0 / c, 0.0))
     return Workload("skin_effect_1d", model, (1, 1, nz), int(periods * period), sigma=sig, sources=[src])
+
+
+# Mesh-refinement sizes of the batched skin-effect sweep: N = 16 k for k = 2 .. 17 (32 ... 272).
+REFINEMENT_SIZES = tuple(16 * k for k in range(2, 18))
+
+
+def skin_effect_3d(model: str, n: int, sigma: float, e0: float = 1e-4) -> Workload:
+    """Section IV-B on an n^3 lattice: conductor (sigma) for z >= n/4, plane wave E_x = e0 sin(2 pi t /
+    T), B_y = E_x / C imposed on the whole z = 0 plane, T = 1.25 n, 10 n steps. Media and source are
+    uniform in x and y, so every (x, y) column evolves like the 1 x 1 x n lattice."""
+    cells_per_plane = n * n
+    z = np.repeat(np.arange(n), cells_per_plane)
+    sig = np.where(z >= n // 4, float(sigma), 0.0)
+    period = 1.25 * n
+    c = LIGHT_SPEED[model]
+    src = Source("impose", np.arange(cells_per_plane, dtype=np.int64), TimeFunction("sin", 1.0, period, 0.0),
+                 E0=(e0, 0.0, 0.0), B0=(0.0, e0 / c, 0.0))
+    return Workload("skin_effect_3d", model, (n, n, n), 10 * n, sigma=sig, sources=[src])
+
+
+def refinement_batch(model: str, sigma: float, sizes=REFINEMENT_SIZES) -> list:
+    """The batched skin-effect refinement sweep: one ``skin_effect_3d`` lattice per size."""
+    return [skin_effect_3d(model, n, sigma) for n in sizes]
 
 
 def random_medium_dipole(model: str, n: int = 128, seed: int = 5, period: float = 24.0, j0: float = 1e-4,
