@@ -78,6 +78,9 @@ def _load():
     lib.or_get_populations.argtypes = [P, D]
     lib.or_set_populations.argtypes = [P, D, I64]
     lib.or_tables.argtypes = [P, D, D, D]
+    lib.or_adjoint_step.argtypes = [P, I64, D, D, D, D, D]
+    lib.or_plane_loss.argtypes = [P, I64, D, ctypes.c_int, ctypes.c_int, D, D, D]
+    lib.or_plane_loss.restype = ctypes.c_double
     _lib = lib
     return lib
 
@@ -201,6 +204,40 @@ class OracleLattice:
     def set_populations(self, f, t: int = 0) -> None:
         f = _f64(f, (self.q, self.n))
         self.lib.or_set_populations(self.h, _dptr(f), int(t))
+
+    def adjoint_step(self, iteration: int, g_next, f_n, grad_eps_r=None, grad_sigma=None):
+        """dL/df^n from dL/df^{n+1} through forward iteration `iteration` (sources s(iteration)),
+        adding dL/d eps_r and dL/d sigma into the given float64 arrays (n values each)."""
+        g_next = _f64(g_next, (self.q, self.n))
+        f_n = _f64(f_n, (self.q, self.n))
+        out = np.empty((self.q, self.n), dtype=np.float64)
+        self.lib.or_adjoint_step(self.h, int(iteration), _dptr(g_next), _dptr(f_n), _dptr(out), _dptr(grad_eps_r),
+                                 _dptr(grad_sigma))
+        return out
+
+    def plane_loss(self, t: int, f_t, axis: int, index: int, g=None, grad_eps_r=None, grad_sigma=None) -> float:
+        """sum over the plane cells of |E(f_t)|^2 at time t; adds its derivatives when arrays are given."""
+        f_t = _f64(f_t, (self.q, self.n))
+        return float(self.lib.or_plane_loss(self.h, int(t), _dptr(f_t), int(axis), int(index), _dptr(g),
+                                            _dptr(grad_eps_r), _dptr(grad_sigma)))
+
+    def loss_and_gradient(self, steps: int, axis: int, index: int):
+        """From the current state: run `steps` steps, return L = sum_{t=1..steps} plane_loss(t) and
+        dL/d eps_r, dL/d sigma by the adjoint recursion (all states kept; small lattices only)."""
+        t0 = self.time
+        states = [self.populations()]
+        for _ in range(steps):
+            self.step(1)
+            states.append(self.populations())
+        ge = np.zeros(self.n)
+        gs = np.zeros(self.n)
+        g = np.zeros((self.q, self.n))
+        loss = self.plane_loss(t0 + steps, states[steps], axis, index, g, ge, gs)
+        for k in range(steps - 1, -1, -1):
+            g = self.adjoint_step(t0 + k + 1, g, states[k], ge, gs)
+            if k >= 1:
+                loss += self.plane_loss(t0 + k, states[k], axis, index, g, ge, gs)
+        return loss, ge, gs
 
     def tables(self):
         v = np.zeros((12, 3))

@@ -594,3 +594,141 @@ void or_tables(const or_lattice *L, double *v, double *e, double *b) {
             for (int a = 0; a < 3; ++a) v[i * 3 + a] = L->hv_v[i][a];
     }
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Adjoint of one time step (for gradients of a loss with respect to eps_r and sigma)           */
+/* ------------------------------------------------------------------------------------------ */
+/*
+ * One forward iteration maps the pre-collision populations f^n to f^{n+1}: collide every cell
+ * (affine in its own populations), then advect f^{n+1}(x + v_k)[k] = f'(x)[k]. Given
+ * g_next = dL/df^{n+1} (canonical layout), or_adjoint_step returns g_out = dL/df^n through this step
+ * and adds dL/d eps_r and dL/d sigma of every cell.
+ *
+ * The transpose is taken by probing the oracle's own collision, not by a separate derivation:
+ *   - the adjoint of the post-collision values of cell x is g_next(x + v_k)[k] (advection reversed);
+ *   - column k of the collision's Jacobian is collide(unit k) - collide(0), so
+ *     g_out(x)[k] = sum_m gp[m] * (collide(unit k)[m] - collide(0)[m]);
+ *   - d collide / d eps_r and d collide / d sigma at f^n(x) are central differences in double
+ *     precision (step 1e-6 relative), contracted with gp.
+ * iter is the forward iteration number (its sources are s(iter)).
+ */
+static void collide_at(or_lattice *L, int64_t x, const double *f, double *out) {
+    if (L->model == OR_MM) mm_collide(L, x, f, out);
+    else hv_collide(L, x, f, out);
+}
+
+void or_adjoint_step(or_lattice *L, int64_t iter, const double *g_next, const double *f_n, double *g_out,
+                     double *grad_eps_r, double *grad_sigma) {
+    const int q = L->q;
+    const int64_t n = L->n;
+    int vel[50][3];
+    for (int k = 0; k < q; ++k) velocity_of(L, k, vel[k]);
+    if (L->nsrc > 0) evaluate_sources(L, iter);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(L->nthreads)
+#endif
+    for (int z = 0; z < L->nz; ++z) {
+        double gp[50], f[50], unit[50], base[50], probe[50], plus[50], minus[50];
+        for (int y = 0; y < L->ny; ++y)
+            for (int x = 0; x < L->nx; ++x) {
+                int64_t c = cell_index(L, x, y, z);
+                for (int k = 0; k < q; ++k) {
+                    int64_t d = cell_index(L, x + vel[k][0], y + vel[k][1], z + vel[k][2]);
+                    gp[k] = g_next[(int64_t)k * n + d];
+                    f[k] = f_n[(int64_t)k * n + c];
+                    unit[k] = 0.0;
+                }
+                collide_at(L, c, unit, base);
+                for (int k = 0; k < q; ++k) {
+                    unit[k] = 1.0;
+                    collide_at(L, c, unit, probe);
+                    unit[k] = 0.0;
+                    double s = 0.0;
+                    for (int m = 0; m < q; ++m) s += gp[m] * (probe[m] - base[m]);
+                    g_out[(int64_t)k * n + c] = s;
+                }
+                double *param[2] = {&L->eps_r[c], &L->sigma[c]};
+                double *grad[2] = {grad_eps_r, grad_sigma};
+                for (int p = 0; p < 2; ++p) {
+                    if (!grad[p]) continue;
+                    double v0 = *param[p];
+                    double h = 1e-6 * (fabs(v0) > 1e-3 ? fabs(v0) : 1e-3);
+                    *param[p] = v0 + h;
+                    collide_at(L, c, f, plus);
+                    *param[p] = v0 - h;
+                    collide_at(L, c, f, minus);
+                    *param[p] = v0;
+                    double s = 0.0;
+                    for (int m = 0; m < q; ++m) s += gp[m] * (plus[m] - minus[m]) / (2.0 * h);
+                    grad[p][c] += s;
+                }
+            }
+    }
+}
+
+/* Loss term of one time: L_t = sum over the cells of plane (axis, index) of |E(f, t)|^2, E as in
+ * or_fields (external current of iteration t + 1). Returns L_t; adds dL_t/df to g (canonical) and
+ * dL_t/d eps_r, dL_t/d sigma to the gradients. The derivatives are probed like or_adjoint_step: E is
+ * affine in f, so dE/df_k = E(unit k) - E(0); parameters by central differences. */
+static void fields_at(or_lattice *L, int64_t x, const double *f, double E[3]) {
+    static const double zero3[3] = {0.0, 0.0, 0.0};
+    const double *jext = L->jext ? &L->jext[3 * x] : zero3;
+    if (L->model == OR_MM) {
+        double Dp[3], B[3], rho, J[3];
+        mm_moments(L, f, Dp, B, &rho);
+        mm_e_and_j(L, x, Dp, jext, E, J);
+    } else {
+        double D[3], B[3], eps = L->eps0 * L->eps_r[x];
+        hv_moments(f, D, B);
+        for (int a = 0; a < 3; ++a) E[a] = D[a] / eps;
+    }
+}
+
+double or_plane_loss(or_lattice *L, int64_t t, const double *f_t, int axis, int index, double *g, double *grad_eps_r,
+                     double *grad_sigma) {
+    const int q = L->q;
+    const int64_t n = L->n;
+    if (L->nsrc > 0) evaluate_sources(L, t + 1);
+    double loss = 0.0;
+    for (int z = 0; z < L->nz; ++z)
+        for (int y = 0; y < L->ny; ++y)
+            for (int x = 0; x < L->nx; ++x) {
+                int coord = axis == 0 ? x : (axis == 1 ? y : z);
+                if (coord != index) continue;
+                int64_t c = cell_index(L, x, y, z);
+                double f[50], unit[50], E[3], E0[3], Ek[3];
+                for (int k = 0; k < q; ++k) {
+                    f[k] = f_t[(int64_t)k * n + c];
+                    unit[k] = 0.0;
+                }
+                fields_at(L, c, f, E);
+                loss += E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
+                if (g) {
+                    fields_at(L, c, unit, E0);
+                    for (int k = 0; k < q; ++k) {
+                        unit[k] = 1.0;
+                        fields_at(L, c, unit, Ek);
+                        unit[k] = 0.0;
+                        double s = 0.0;
+                        for (int a = 0; a < 3; ++a) s += 2.0 * E[a] * (Ek[a] - E0[a]);
+                        g[(int64_t)k * n + c] += s;
+                    }
+                }
+                double *param[2] = {&L->eps_r[c], &L->sigma[c]};
+                double *grad[2] = {grad_eps_r, grad_sigma};
+                for (int p = 0; p < 2; ++p) {
+                    if (!grad[p]) continue;
+                    double v0 = *param[p], Ep[3], Em[3];
+                    double h = 1e-6 * (fabs(v0) > 1e-3 ? fabs(v0) : 1e-3);
+                    *param[p] = v0 + h;
+                    fields_at(L, c, f, Ep);
+                    *param[p] = v0 - h;
+                    fields_at(L, c, f, Em);
+                    *param[p] = v0;
+                    double s = 0.0;
+                    for (int a = 0; a < 3; ++a) s += 2.0 * E[a] * (Ep[a] - Em[a]) / (2.0 * h);
+                    grad[p][c] += s;
+                }
+            }
+    return loss;
+}
