@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -254,6 +255,58 @@ def refinement_sweep(stream, steps: int):
     return out
 
 
+def adjoint_cost(stream, steps: int):
+    """Inverse-design workload: 128^3 lattice, per-cell eps_r uniform in [1, 4), dipole with period
+    24, loss plane x = 100. Time `steps` forward steps, then lbm_adjoint over `steps` steps from the
+    same start in its two modes: every step's record resident in HBM (interval -1), and checkpoints
+    every ceil(sqrt(steps)) steps with one recomputation per segment. Wall time of the whole call per
+    step, against the forward step: the first call allocates the work space, the second (reported)
+    reuses it."""
+    import torch
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    out = {}
+    k_sqrt = int(math.ceil(math.sqrt(steps)))
+    for model in ("mm", "hv"):
+        w = wl.random_medium_dipole(model, n=128, steps=steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            L = lattice_from_workload(w, stream=stream)
+        L.step(3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / steps
+        L.close()
+        res = {"cells": w.n, "steps": steps, "forward_ms_per_step": round(fwd_ms, 4)}
+        losses = []
+        for mode, interval in (("resident", -1), (f"checkpoint_{k_sqrt}", k_sqrt)):
+            with torch.cuda.stream(stream):
+                L = lattice_from_workload(w, stream=stream)
+            torch.cuda.synchronize()
+            # first call: allocates the work space; second: reuses it, as an optimisation loop does
+            calls = []
+            for call in range(2):
+                t0 = time.perf_counter()
+                loss, ge, _ = L.adjoint(steps, 0, 100, interval)
+                calls.append((time.perf_counter() - t0) * 1e3 / steps)
+                if call == 0:
+                    losses.append(loss)  # both modes start from the same state here
+            first_ms, adj_ms = calls
+            res[mode] = {"adjoint_ms_per_step": round(adj_ms, 4), "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
+                         "first_call_ms_per_step": round(first_ms, 4),
+                         "workspace_gb": round(L.adjoint_workspace_bytes / 1e9, 3),
+                         "gradient_finite": bool(torch.isfinite(ge).all().item())}
+            L.close()
+            del ge
+            torch.cuda.empty_cache()
+        res["loss"] = losses[0]
+        res["modes_agree"] = losses[0] == losses[1]
+        out[model] = res
+    return out
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -372,6 +425,7 @@ def run_ours(args):
             Lv.close()
     accuracy = storage_accuracy() if rank == 0 else None
     refinement = refinement_sweep(stream, args.refine_steps) if args.refine_steps > 0 else None
+    adjoint = adjoint_cost(stream, args.adjoint_steps) if args.adjoint_steps > 0 else None
 
     # end to end through the C ABI with host buffers: upload fields, K steps, read E and B back
     pinned_E = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
@@ -440,6 +494,7 @@ def run_ours(args):
             for st in variants},
         "rel_l2_vs_fp64_dielectric_pulse_1500": accuracy,
         "refinement_batch": refinement,
+        "adjoint": adjoint,
         "gpu_launches": int(launches),
         "finite": finite,
         "clocks": clocks.summary(),
@@ -458,6 +513,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--adjoint-steps", type=int, default=1000,
+                    help="steps of the adjoint-cost measurement on the 128^3 random medium (0 skips it)")
     ap.add_argument("--refine-steps", type=int, default=100,
                     help="steps of the batched refinement-sweep measurement (0 skips it)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",

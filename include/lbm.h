@@ -198,6 +198,33 @@ int lbm_sync(lbm_ctx* ctx);
 /* Free the context and its device memory. NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);
 
+/* Loss and gradient over the next `steps` time steps (inverse material design; the paper itself
+ * only runs forward). From the current populations, the context advances `steps` steps exactly as
+ * lbm_step does, and
+ *   L = sum_{t=1..steps} sum over the cells of plane (plane_axis, plane_index) of |E(t)|^2,
+ * with E(t) the field lbm_fields reports after t steps. The gradients dL/d eps_r and dL/d sigma of
+ * every cell (n floats each; NULL skips one) are taken at fixed starting populations. The adjoint
+ * steps back through the transposed collide-and-stream map. What it needs of forward step t is a
+ * per-cell record: E and X = D' - mu0 J_ext / 4 for MM (24 bytes per cell), E for HV (12 bytes).
+ *   checkpoint_interval < 0: the forward pass keeps every step's record in device memory
+ *     (steps x record bytes); the backward pass recomputes nothing.
+ *   checkpoint_interval > 0: population states are kept every checkpoint_interval steps, and each
+ *     segment is recomputed once, writing its records, before it is stepped back through.
+ *   checkpoint_interval == 0: the first mode when the records take at most half the free device
+ *     memory, else the second with interval ceil(sqrt(steps)).
+ * Every mode gives the same loss and gradients, bit for bit. Needs FP32 storage; source cells must
+ * not lie in the plane (LBM_EINVAL). loss_out is a host double; gradient outputs are host
+ * (on_device = 0) or device memory. The work space (records or checkpoints, two adjoint states, the
+ * gradient sums) is allocated on the first call, LBM_ENOMEM when it does not fit, and kept by the
+ * context for later calls, which grow it when they need more; lbm_adjoint_release or lbm_destroy
+ * frees it. Waits for the stream. */
+int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_index, int checkpoint_interval, double* loss_out,
+                float* grad_eps_r, float* grad_sigma, int on_device);
+/* Free the work space lbm_adjoint keeps (after waiting for the stream). */
+int lbm_adjoint_release(lbm_ctx* ctx);
+/* Bytes of device memory held as lbm_adjoint work space (0 when none; -1 for NULL). */
+int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx);
+
 /* ---------------------------------------------------------------------------------------------
  * Batched stepping of lattices of uneven sizes. The paper's studies are mesh-refinement sweeps:
  * the same test on lattices refined step by step (Section IV, "for different refinements of the

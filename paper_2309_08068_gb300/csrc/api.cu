@@ -70,6 +70,9 @@ struct lbm_ctx {
     double* d_result = nullptr;
     int reduce_blocks = 0;
     int partial_capacity = 0;  // blocks
+    // adjoint work space (records, checkpoints, adjoint states), kept between lbm_adjoint calls
+    void* adj_ws = nullptr;
+    size_t adj_ws_bytes = 0;
     int64_t t = 0;
     int64_t launches = 0;
     std::string err;
@@ -370,6 +373,8 @@ void release(lbm_ctx* c) {
     free_sources_device(c);
     free_dev(c->d_partials);
     free_dev(c->d_result);
+    free_dev(c->adj_ws);
+    c->adj_ws_bytes = 0;
 }
 
 // Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
@@ -748,6 +753,20 @@ __global__ void __launch_bounds__(kBlock) reduce_partials_kernel(const double* _
 
 int launch_reduce_partials(const double* partials, int n_blocks, double* result, cudaStream_t st) {
     reduce_partials_kernel<<<1, kBlock, 0, st>>>(partials, n_blocks, result);
+    return 1;
+}
+
+namespace {
+__global__ void __launch_bounds__(kBlock) sum_doubles_kernel(const double* __restrict__ v, int count,
+                                                             double* __restrict__ result) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < count; k += kBlock) s += v[k];
+    block_sum3_store(s, 0.0, 0.0, result);
+}
+}  // namespace
+
+int launch_sum_doubles(const double* v, int count, double* result, cudaStream_t st) {
+    sum_doubles_kernel<<<1, kBlock, 0, st>>>(v, count, result);
     return 1;
 }
 }  // namespace lbm
@@ -1180,3 +1199,220 @@ int lbm_batch_destroy(lbm_batch* b) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// lbm_adjoint: loss over the next T steps and its gradient with respect to eps_r and sigma.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+// Carves 256-byte-aligned pieces out of one allocation, in a fixed order.
+struct Arena {
+    size_t used = 0;
+    char* base = nullptr;
+    char* take(size_t bytes) {
+        const size_t at = (used + 255) & ~(size_t)255;
+        used = at + bytes;
+        return base ? base + at : nullptr;
+    }
+};
+
+int plane_size(const lbm_ctx* c, int axis) {
+    return axis == 0 ? c->g.ny * c->g.nz : (axis == 1 ? c->g.nx * c->g.nz : c->g.nx * c->g.ny);
+}
+
+}  // namespace
+
+extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_index, int checkpoint_interval,
+                           double* loss_out, float* grad_eps_r, float* grad_sigma, int on_device) {
+    if (!ctx) return LBM_EINVAL;
+    if (steps < 1) return fail(ctx, LBM_EINVAL, "lbm_adjoint: steps must be >= 1");
+    if (!loss_out) return fail(ctx, LBM_EINVAL, "lbm_adjoint: loss_out is NULL");
+    if (ctx->storage != LBM_F32) return fail(ctx, LBM_EUNSUPPORTED, "lbm_adjoint: needs FP32 population storage");
+    const int dims[3] = {ctx->g.nx, ctx->g.ny, ctx->g.nz};
+    if (plane_axis < 0 || plane_axis > 2 || plane_index < 0 || plane_index >= dims[plane_axis])
+        return fail(ctx, LBM_EINVAL, "lbm_adjoint: plane (axis %d, index %d) outside the lattice", plane_axis,
+                    plane_index);
+    for (const HostSource& s : ctx->sources)
+        for (int cell : s.cells) {
+            const int x = cell % ctx->g.nx, y = (cell / ctx->g.nx) % ctx->g.ny, z = cell / (ctx->g.nx * ctx->g.ny);
+            const int coord = plane_axis == 0 ? x : (plane_axis == 1 ? y : z);
+            if (coord == plane_index)
+                return fail(ctx, LBM_EINVAL, "lbm_adjoint: source cell %d lies in the loss plane", cell);
+        }
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    const int64_t n = ctx->g.n;
+    const size_t b1 = group_bytes(ctx->model, ctx->storage) * (size_t)n;
+    const size_t b2 = ctx->model == LBM_HV ? pair_bytes(ctx->storage) * (size_t)n : 0;
+    const size_t state = b1 + b2;
+    const size_t rec_bytes = sizeof(float) * (size_t)n * (ctx->model == LBM_MM ? kRecordFloatsMM : kRecordFloatsHV);
+    const int n_plane = plane_size(ctx, plane_axis);
+    // Work space of a layout with K record slots and n_ck checkpoints (K = steps, n_ck = 0: resident).
+    struct Layout {
+        char *recs, *ck, *work, *nu, *mask, *loss;
+        float *g_eps, *g_sig;
+    };
+    auto layout = [&](char* base, int K, int n_ck, Layout* L) {
+        Arena a;
+        a.base = base;
+        L->recs = a.take(rec_bytes * (size_t)K);
+        L->ck = a.take(state * (size_t)n_ck);
+        L->work = a.take(n_ck > 0 ? state * 2 : 0);
+        L->nu = a.take(state * 2);
+        L->g_eps = reinterpret_cast<float*>(a.take(sizeof(float) * (size_t)n));
+        L->g_sig = reinterpret_cast<float*>(a.take(sizeof(float) * (size_t)n));
+        L->mask = a.take((size_t)n);
+        L->loss = a.take(sizeof(double) * ((size_t)n_plane + 3));
+        return a.used;
+    };
+    // Mode: every step's record resident in device memory (no recomputation) when asked for
+    // (interval < 0) or, automatically (interval == 0), when that work space fits in half the free
+    // memory; otherwise checkpoints of the state every K steps and one recomputation per segment.
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
+    const size_t avail = free_b + ctx->adj_ws_bytes;
+    Layout Ly;
+    const size_t resident_bytes = layout(nullptr, steps, 0, &Ly);
+    const bool resident = checkpoint_interval < 0 || (checkpoint_interval == 0 && resident_bytes <= avail / 2);
+    const int K = resident ? steps
+                           : (checkpoint_interval > 0 ? checkpoint_interval
+                                                      : std::max(1, (int)std::ceil(std::sqrt((double)steps))));
+    const int n_ck = resident ? 0 : (steps + K - 1) / K;
+    const size_t need = layout(nullptr, K, n_ck, &Ly);
+    if (need > ctx->adj_ws_bytes) {
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        free_dev(ctx->adj_ws);
+        ctx->adj_ws_bytes = 0;
+        if (cudaMalloc(&ctx->adj_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->adj_ws = nullptr;
+            return fail(ctx, LBM_ENOMEM, "lbm_adjoint: cannot allocate %zu bytes of work space (%s, interval %d)",
+                        need, resident ? "resident records" : "checkpoints", K);
+        }
+        ctx->adj_ws_bytes = need;
+    }
+    layout(static_cast<char*>(ctx->adj_ws), K, n_ck, &Ly);
+    CUDA_TRY(ctx, cudaMemsetAsync(Ly.g_eps, 0, sizeof(float) * (size_t)n, ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(Ly.g_sig, 0, sizeof(float) * (size_t)n, ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(Ly.mask, 0, (size_t)n, ctx->stream));
+    if (ctx->n_special > 0) {
+        std::vector<uint8_t> m((size_t)n, 0);
+        for (const HostSource& s : ctx->sources)
+            for (int cell : s.cells) m[(size_t)cell] = 1;
+        CUDA_TRY(ctx, cudaMemcpyAsync(Ly.mask, m.data(), (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // m is released on return
+    }
+    auto state_ptrs = [&](char* base, void** p1, void** p2) {
+        *p1 = base;
+        *p2 = b2 ? base + b1 : nullptr;
+    };
+    // One forward step between explicit states, writing the adjoint record when rec is given. The
+    // context's own pass also steps MM's tracked rest populations (it ends where lbm_step would).
+    auto forward = [&](void* in1, void* in2, void* out1, void* out2, int64_t iter, bool own_state, void* rec) {
+        StepArgs a = base_args(ctx);
+        a.fin = in1;
+        a.fin2 = in2;
+        a.fout = out1;
+        a.fout2 = out2;
+        a.rho_in = own_state ? ctx->rho[ctx->cur] : nullptr;
+        a.rho_out = own_state ? ctx->rho[1 - ctx->cur] : nullptr;
+        a.rec = static_cast<float*>(rec);
+        fill_scalars(ctx, a, iter);
+        if (rec)
+            return ctx->model == LBM_MM ? mm_launch_record_step(a, ctx->stream) : hv_launch_record_step(a, ctx->stream);
+        return ctx->model == LBM_MM ? mm_launch_step(a, ctx->stream) : hv_launch_step(a, ctx->stream);
+    };
+    int64_t launched = 0;
+    const int64_t t0 = ctx->t;
+    // Forward pass: records (resident mode) or checkpoints.
+    for (int s = 0; s < steps; ++s) {
+        void* in1 = ctx->buf[ctx->cur];
+        void* in2 = ctx->buf2[ctx->cur];
+        if (!resident && s % K == 0) {
+            char* slot = Ly.ck + state * (size_t)(s / K);
+            CUDA_TRY(ctx, cudaMemcpyAsync(slot, in1, b1, cudaMemcpyDeviceToDevice, ctx->stream));
+            if (b2) CUDA_TRY(ctx, cudaMemcpyAsync(slot + b1, in2, b2, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        launched += forward(in1, in2, ctx->buf[1 - ctx->cur], ctx->buf2[1 - ctx->cur], t0 + s + 1, true,
+                            resident ? Ly.recs + rec_bytes * (size_t)s : nullptr);
+        ctx->cur = 1 - ctx->cur;
+        ctx->t += 1;
+    }
+    if ((rc = check_launch(ctx, (int)launched)) != LBM_OK) return rc;
+    launched = 0;
+    // Terminal adjoint: nu^T = dL_T / df^T on the plane, and |E(T)|^2, from the final state.
+    double* loss_plane = reinterpret_cast<double*>(Ly.loss);
+    double* loss_dev = loss_plane + n_plane;
+    int nu_cur = 0;
+    CUDA_TRY(ctx, cudaMemsetAsync(Ly.nu, 0, state, ctx->stream));
+    AdjointArgs A;
+    memset(&A, 0, sizeof(A));
+    A.grad_eps = Ly.g_eps;
+    A.grad_sigma = Ly.g_sig;
+    A.special_mask = reinterpret_cast<const uint8_t*>(Ly.mask);
+    A.plane_axis = plane_axis;
+    A.plane_index = plane_index;
+    A.loss_plane = loss_plane;
+    A.a = base_args(ctx);
+    A.a.fin = ctx->buf[ctx->cur];
+    A.a.fin2 = ctx->buf2[ctx->cur];
+    fill_scalars(ctx, A.a, t0 + steps + 1);
+    state_ptrs(Ly.nu, &A.nu_out, &A.nu_out2);
+    A.loss_active = 1;
+    launched += ctx->model == LBM_MM ? mm_launch_adjoint_terminal(A, n_plane, ctx->stream)
+                                     : hv_launch_adjoint_terminal(A, n_plane, ctx->stream);
+    // Backward through one run of records (those of steps first .. first + len - 1).
+    auto backward = [&](int first, int len) {
+        for (int j = len - 1; j >= 0; --j) {
+            const int64_t nstep = first + j;  // reverses forward iteration nstep + 1
+            A.a = base_args(ctx);
+            A.a.rec = reinterpret_cast<float*>(Ly.recs + rec_bytes * (size_t)(resident ? nstep : j));
+            fill_scalars(ctx, A.a, t0 + nstep + 1);
+            state_ptrs(Ly.nu + state * (size_t)nu_cur, const_cast<void**>(&A.nu_in), const_cast<void**>(&A.nu_in2));
+            state_ptrs(Ly.nu + state * (size_t)(1 - nu_cur), &A.nu_out, &A.nu_out2);
+            A.loss_active = nstep >= 1 ? 1 : 0;
+            launched += ctx->model == LBM_MM ? mm_launch_adjoint(A, ctx->stream) : hv_launch_adjoint(A, ctx->stream);
+            nu_cur = 1 - nu_cur;
+        }
+    };
+    if (resident) {
+        backward(0, steps);
+    } else {
+        for (int k = n_ck - 1; k >= 0; --k) {
+            const int first = k * K, len = std::min(K, steps - first);
+            // Recompute the segment from its checkpoint through two scratch states, recording each step.
+            void *i1, *i2, *o1, *o2;
+            state_ptrs(Ly.ck + state * (size_t)k, &i1, &i2);
+            for (int j = 0; j < len; ++j) {
+                state_ptrs(Ly.work + state * (size_t)(j & 1), &o1, &o2);
+                launched += forward(i1, i2, o1, o2, t0 + first + j + 1, false, Ly.recs + rec_bytes * (size_t)j);
+                i1 = o1;
+                i2 = o2;
+            }
+            backward(first, len);
+        }
+    }
+    launched += launch_sum_doubles(loss_plane, n_plane, loss_dev, ctx->stream);
+    if ((rc = check_launch(ctx, (int)launched)) != LBM_OK) return rc;
+    CUDA_TRY(ctx, cudaMemcpyAsync(loss_out, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (grad_eps_r)
+        CUDA_TRY(ctx, cudaMemcpyAsync(grad_eps_r, Ly.g_eps, sizeof(float) * n,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (grad_sigma)
+        CUDA_TRY(ctx, cudaMemcpyAsync(grad_sigma, Ly.g_sig, sizeof(float) * n,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_release(lbm_ctx* ctx) {
+    if (!ctx) return LBM_EINVAL;
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    free_dev(ctx->adj_ws);
+    ctx->adj_ws_bytes = 0;
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx) { return ctx ? (int64_t)ctx->adj_ws_bytes : -1; }

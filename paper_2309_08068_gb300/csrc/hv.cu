@@ -117,7 +117,7 @@ __device__ __forceinline__ float3 hv_h(float3 B, const MatCoef& mat) {
 }
 
 // Update of cell i; m is its index in the special-cell list when kSpecial.
-template <int S, int M, bool kSpecial>
+template <int S, int M, bool kSpecial, bool kRecord = false>
 __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m) {
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 e[6];
@@ -157,6 +157,12 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m) {
         }
         hv_put<S>(a, k, i, make_float4(eo.x, eo.y, eo.z, ho.x), make_float2(ho.y, ho.z));
     });
+    if constexpr (kRecord) {  // what the adjoint of this step needs: E
+        const int n = a.g.n;
+        a.rec[i] = F.E.x;
+        a.rec[n + i] = F.E.y;
+        a.rec[2 * n + i] = F.E.z;
+    }
 }
 
 template <int S, int M, bool kSpecial>
@@ -329,6 +335,151 @@ __global__ void __launch_bounds__(kBlock) hv_batch_special_kernel(const BatchLat
     }
 }
 
+template <int M, bool kSpecial>
+__global__ void __launch_bounds__(kBlock) hv_record_kernel(StepArgs a) {
+    if constexpr (kSpecial) {
+        const int m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        hv_update<kF32, M, true, true>(a, a.sv.cell[m], m);
+    } else {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+        hv_update<kF32, M, false, true>(a, i, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint of one HV step. With adjoints e_i^, h_i^ of the post-collision vectors, the transpose of
+// e_i' = D/3 - v_i x H - e_i - (J . v_i) v_i / 2 and h_i' = B/3 + v_i x E - h_i is
+//   gH = sum_i v_i x e_i^,   gE = sum_i h_i^ x v_i + sigma gJ,   gJ_a = -(1/2) sum_{i on axis a} e_i^_a,
+//   gD = sum_i e_i^ / 3 + gE / eps,   gB = sum_i h_i^ / 3 + gH / mu,
+//   nu(e_i) = gD - e_i^,   nu(h_i) = gB - h_i^,
+//   dL/d eps_r += -gE . E / eps_r   (E = D / (eps0 eps_r)),   dL/d sigma += gJ . E.
+// Imposed cells output f_eq(E_imp, B_imp, 0), where D_imp = eps0 eps_r E_imp: nothing flows back
+// to f, and d e_i' / d eps_r = eps0 E_imp / 6. The plane loss |E|^2 adds 2E to gE.
+template <int M, bool kSpecial, bool kTerminal>
+__device__ __forceinline__ void hv_adjoint_cell(const AdjointArgs& A, int i, int m) {
+    const StepArgs& a = A.a;
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, i);
+    const MatCoef mat = load_coef<kModelHV, M>(a.media, i, a.eps0, a.mu0);
+    CellSource cs;
+    bool imposed = false;
+    if constexpr (kSpecial) {
+        cs = cell_source(a.sv, a.sc, m);
+        imposed = cs.imposed;
+    }
+    // Every load is issued up front: the source-cell mask of the main launch only gates the stores,
+    // so it adds no round trip before the others.
+    const bool skip = !kSpecial && !kTerminal && A.special_mask[i] != 0;
+    const float geps_old = __ldg(&A.grad_eps[i]), gsig_old = __ldg(&A.grad_sigma[i]);
+    // E of f^n: from the forward step's record, or (terminal) from the final state
+    float3 E;
+    if constexpr (kTerminal) {
+        float4 e[6];
+        float2 hy[6];
+        hv_pull<kF32>(a, h, e, hy);
+        E = hv_fields(e, hy, mat, make_float3(0.f, 0.f, 0.f)).E;
+    } else {
+        E = make_float3(__ldg(&a.rec[i]), __ldg(&a.rec[n + i]), __ldg(&a.rec[2 * n + i]));
+    }
+    struct {
+        float3 E;
+    } F{E};
+    const float inv_eps = mat.c0.y, inv_mu = mat.c0.w, sigma = mat.c1.x, er = mat.c1.y;
+    float4 le[6];
+    float2 lh[6];
+    static_for<0, 6>([&](auto ic) {
+        constexpr int k = decltype(ic)::value;
+        if constexpr (kTerminal) {
+            le[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            lh[k] = make_float2(0.f, 0.f);
+        } else {
+            const int dst = push_index<k>(h);
+            le[k] = __ldg(static_cast<const float4*>(A.nu_in) + (size_t)k * n + dst);
+            lh[k] = __ldg(static_cast<const float2*>(A.nu_in2) + (size_t)k * n + dst);
+        }
+    });
+    float3 Se = make_float3(0.f, 0.f, 0.f), Sh = Se, gH = Se, gE = Se, gJ = Se;
+    float geps_imposed = 0.f;
+    if (!imposed) {
+        static_for<0, 6>([&](auto ic) {
+            constexpr int k = decltype(ic)::value;
+            constexpr int AX = kHVAxis[k], G = kHVSign[k];
+            const float3 ek = make_float3(le[k].x, le[k].y, le[k].z);
+            const float3 hk = make_float3(le[k].w, lh[k].x, lh[k].y);
+            Se = make_float3(Se.x + ek.x, Se.y + ek.y, Se.z + ek.z);
+            Sh = make_float3(Sh.x + hk.x, Sh.y + hk.y, Sh.z + hk.z);
+            const float3 ve = axis_cross<AX, G>(ek);  // v_k x e_k^
+            const float3 vh = axis_cross<AX, G>(hk);  // v_k x h_k^ = -(h_k^ x v_k)
+            gH = make_float3(gH.x + ve.x, gH.y + ve.y, gH.z + ve.z);
+            gE = make_float3(gE.x - vh.x, gE.y - vh.y, gE.z - vh.z);
+            if constexpr (AX == 0) gJ.x -= 0.5f * ek.x;
+            else if constexpr (AX == 1) gJ.y -= 0.5f * ek.y;
+            else gJ.z -= 0.5f * ek.z;
+        });
+        gE = make_float3(__fmaf_rn(sigma, gJ.x, gE.x), __fmaf_rn(sigma, gJ.y, gE.y), __fmaf_rn(sigma, gJ.z, gE.z));
+    } else if constexpr (kSpecial) {
+        const float3 dE = make_float3(div_rn(a.eps0 * cs.E.x, 6.f, kInv6), div_rn(a.eps0 * cs.E.y, 6.f, kInv6),
+                                      div_rn(a.eps0 * cs.E.z, 6.f, kInv6));
+        static_for<0, 6>([&](auto ic) {
+            constexpr int k = decltype(ic)::value;
+            geps_imposed += le[k].x * dE.x + le[k].y * dE.y + le[k].z * dE.z;
+        });
+    }
+    if (A.loss_active && in_plane(h, a.g, A.plane_axis, A.plane_index)) {  // |E|^2 of time n
+        gE = make_float3(__fmaf_rn(2.f, F.E.x, gE.x), __fmaf_rn(2.f, F.E.y, gE.y), __fmaf_rn(2.f, F.E.z, gE.z));
+        add_plane_loss<kTerminal>(A, h, F.E);
+    }
+    const float3 gD = make_float3(__fmaf_rn(gE.x, inv_eps, div_rn(Se.x, 3.f, kInv3)),
+                                  __fmaf_rn(gE.y, inv_eps, div_rn(Se.y, 3.f, kInv3)),
+                                  __fmaf_rn(gE.z, inv_eps, div_rn(Se.z, 3.f, kInv3)));
+    const float3 gB = make_float3(__fmaf_rn(gH.x, inv_mu, div_rn(Sh.x, 3.f, kInv3)),
+                                  __fmaf_rn(gH.y, inv_mu, div_rn(Sh.y, 3.f, kInv3)),
+                                  __fmaf_rn(gH.z, inv_mu, div_rn(Sh.z, 3.f, kInv3)));
+    if (skip) return;  // a source cell: the second launch writes it
+    float4* eout = static_cast<float4*>(A.nu_out);
+    float2* hout = static_cast<float2*>(A.nu_out2);
+    static_for<0, 6>([&](auto ic) {
+        constexpr int k = decltype(ic)::value;
+        float4 o;
+        float2 p;
+        if (imposed) {
+            o = make_float4(gD.x, gD.y, gD.z, gB.x);
+            p = make_float2(gB.y, gB.z);
+        } else {
+            o = make_float4(gD.x - le[k].x, gD.y - le[k].y, gD.z - le[k].z, gB.x - le[k].w);
+            p = make_float2(gB.y - lh[k].x, gB.z - lh[k].y);
+        }
+        eout[(size_t)k * n + i] = o;
+        hout[(size_t)k * n + i] = p;
+    });
+    const float gEdotE = gE.x * F.E.x + gE.y * F.E.y + gE.z * F.E.z;
+    A.grad_eps[i] = geps_old + (geps_imposed - div_rn(gEdotE, er, 1.f / er));
+    A.grad_sigma[i] = gsig_old + (gJ.x * F.E.x + gJ.y * F.E.y + gJ.z * F.E.z);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock) hv_adjoint_kernel(AdjointArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.a.g.n) return;
+    hv_adjoint_cell<M, false, false>(A, i, 0);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock) hv_adjoint_special_kernel(AdjointArgs A) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= A.a.sv.n_special) return;
+    hv_adjoint_cell<M, true, false>(A, A.a.sv.cell[m], m);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock) hv_adjoint_terminal_kernel(AdjointArgs A, int n_plane) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_plane) return;
+    hv_adjoint_cell<M, false, true>(A, plane_cell(A.a.g, A.plane_axis, A.plane_index, k), 0);
+}
+
 }  // namespace
 
 int hv_launch_step(const StepArgs& a, cudaStream_t st) {
@@ -425,6 +576,42 @@ int hv_batch_occupancy(int storage, int block) {
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, hv_batch_kernel<S, 256>, 256, 0);
     });
     return blocks;
+}
+
+int hv_launch_adjoint(const AdjointArgs& A, cudaStream_t st) {
+    int launched = 0;
+    with_media(A.a.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        hv_adjoint_kernel<M><<<blocks_for(A.a.g.n), kBlock, 0, st>>>(A);
+        launched = 1;
+        if (A.a.sv.n_special > 0) {
+            hv_adjoint_special_kernel<M><<<blocks_for(A.a.sv.n_special), kBlock, 0, st>>>(A);
+            launched = 2;
+        }
+    });
+    return launched;
+}
+
+int hv_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st) {
+    with_media(A.a.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        hv_adjoint_terminal_kernel<M><<<blocks_for(n_plane), kBlock, 0, st>>>(A, n_plane);
+    });
+    return 1;
+}
+
+int hv_launch_record_step(const StepArgs& a, cudaStream_t st) {
+    int launched = 0;
+    with_media(a.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        hv_record_kernel<M, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+        launched = 1;
+        if (a.sv.n_special > 0) {
+            hv_record_kernel<M, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
+            launched = 2;
+        }
+    });
+    return launched;
 }
 
 }  // namespace lbm

@@ -92,7 +92,12 @@ struct StepArgs {
     int storage;      // StorageKind
     float scale;      // 16-bit storage: stored = f * scale
     float inv_scale;  // 1 / scale
+    float* rec;       // adjoint record of this step (recording kernels only): kRecordFloats[model] x n
 };
+
+// Per-cell record an adjoint step needs from its forward step: MM E and X = D' - mu0 J_ext / 4, HV E.
+constexpr int kRecordFloatsMM = 6;
+constexpr int kRecordFloatsHV = 3;
 
 // Field output: for each selected field a 3 x n block; null pointers are skipped.
 struct FieldsOut {
@@ -231,6 +236,7 @@ __device__ __forceinline__ float pairwise_sum(const float (&t)[N]) {
 // Linear-index contributions of the three coordinates shifted by -1, 0, +1 with periodic wrap.
 struct Neighbourhood {
     int xo[3], yo[3], zo[3];
+    int x, y, z;
 };
 
 __device__ __forceinline__ Neighbourhood neighbourhood(const Geometry& g, int i) {
@@ -240,6 +246,9 @@ __device__ __forceinline__ Neighbourhood neighbourhood(const Geometry& g, int i)
     const int y = (int)(((unsigned long long)(unsigned)r * g.mx) >> (32 + g.kx));
     const int x = r - y * g.nx;
     Neighbourhood h;
+    h.x = x;
+    h.y = y;
+    h.z = z;
     h.xo[0] = x == 0 ? g.nx - 1 : x - 1;
     h.xo[1] = x;
     h.xo[2] = x == g.nx - 1 ? 0 : x + 1;
@@ -427,6 +436,59 @@ struct BatchLaunch {
     bool rho;
 };
 
+// --- adjoint (gradients of a plane loss with respect to eps_r and sigma) ---------------------
+// One backward step reverses the forward iteration n -> n+1. nu^{n+1} = dL/df^{n+1} holds the adjoint
+// of every cell's pre-collision populations (FP32, the population group layout). The adjoint of
+// cell x's post-collision values is nu^{n+1} at x + v_d (advection reversed); the transposed
+// collision gives nu^n(x), plus the derivative of the loss of time n when x lies in the loss plane.
+struct AdjointArgs {
+    StepArgs a;            // media, sources of iteration n + 1; record of the forward step in a.rec
+                           // (the terminal launch reads the final state from a.fin / a.fin2 instead)
+    const void* nu_in;     // nu^{n+1} (null for the terminal launch)
+    const void* nu_in2;    // HV second array
+    void* nu_out;          // nu^n
+    void* nu_out2;
+    float* grad_eps;       // dL/d eps_r per cell, accumulated
+    float* grad_sigma;     // dL/d sigma per cell, accumulated
+    const uint8_t* special_mask;  // non-zero at source cells, which the second launch handles
+    int plane_axis, plane_index;  // loss plane: cells whose coordinate on plane_axis is plane_index
+    int loss_active;              // add the plane loss term of time n
+    double* loss_plane;           // |E|^2 summed over time, per plane cell (slot k as in plane_cell);
+                                  // the terminal launch writes it, the others add
+};
+
+// Cells of the loss plane, and whether a cell lies in it.
+__device__ __forceinline__ int plane_cells(const Geometry& g, int axis) {
+    return axis == 0 ? g.ny * g.nz : (axis == 1 ? g.nx * g.nz : g.nx * g.ny);
+}
+__device__ __forceinline__ int plane_cell(const Geometry& g, int axis, int index, int k) {
+    if (axis == 0) return index + g.nx * k;  // k = y + ny z
+    if (axis == 1) {
+        const int z = k / g.nx, x = k - z * g.nx;
+        return x + g.nx * (index + g.ny * z);
+    }
+    return k + g.nx * g.ny * index;  // k = x + nx y
+}
+// Slot k of a plane cell: the inverse of plane_cell.
+__device__ __forceinline__ int plane_slot(const Neighbourhood& h, const Geometry& g, int axis) {
+    return axis == 0 ? h.y + g.ny * h.z : (axis == 1 ? h.x + g.nx * h.z : h.x + g.nx * h.y);
+}
+__device__ __forceinline__ bool in_plane(const Neighbourhood& h, const Geometry& g, int axis, int index) {
+    if (axis == 0) return h.xo[1] == index;
+    if (axis == 1) return h.yo[1] == index * g.nx;
+    return h.zo[1] == index * g.nx * g.ny;
+}
+
+// |E|^2 of a plane cell into its loss slot: written by the terminal launch (time T), then added by
+// the launch of each earlier time, so every slot sums its times in the order T, T-1, ..., 1.
+template <bool kFirst>
+__device__ __forceinline__ void add_plane_loss(const AdjointArgs& A, const Neighbourhood& h, float3 E) {
+    const double e2 = (double)E.x * E.x + (double)E.y * E.y + (double)E.z * E.z;
+    double* slot = A.loss_plane + plane_slot(h, A.a.g, A.plane_axis);
+    if constexpr (kFirst) *slot = e2;
+    else *slot += e2;
+}
+
 // --- host-side launchers (one set per model) -----------------------------------------------
 // Each returns the number of kernels it enqueued (errors are read with cudaGetLastError).
 int mm_launch_step(const StepArgs& a, cudaStream_t st);
@@ -445,6 +507,8 @@ int hv_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* 
 
 // Deterministic double reduction of per-block partial sums (3 values per block, fixed order).
 int launch_reduce_partials(const double* partials, int n_blocks, double* result, cudaStream_t st);
+// Deterministic sum of v[0..count) into result[0] (one block, fixed order; result[1], [2] are 0).
+int launch_sum_doubles(const double* v, int count, double* result, cudaStream_t st);
 
 // Batched step j: main launch over the first n_tiles tiles, source-cell launch over the first
 // n_stiles special tiles. Returns the number of kernels enqueued.
@@ -453,5 +517,16 @@ int hv_launch_batch_step(const BatchLaunch& b, int j, int n_tiles, int n_stiles,
 // Resident blocks per SM of the main batched kernel for this configuration.
 int mm_batch_occupancy(int storage, int block, bool rho);
 int hv_batch_occupancy(int storage, int block);
+
+// Adjoint launches (FP32 storage). adjoint: main launch over every cell not in special_mask, then
+// the source cells. terminal: nu^T over the loss plane (nu_out must be zeroed first), and the
+// first term of loss_plane. record_step: a forward step that also writes the adjoint record of
+// every cell into a.rec.
+int mm_launch_record_step(const StepArgs& a, cudaStream_t st);
+int hv_launch_record_step(const StepArgs& a, cudaStream_t st);
+int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
+int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st);
+int hv_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
+int hv_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st);
 
 }  // namespace lbm

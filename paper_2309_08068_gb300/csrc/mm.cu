@@ -46,6 +46,7 @@ __device__ __forceinline__ float sdot(float x, float y, float z) {
 }
 
 struct MMFields {
+    float3 X;    // D' - mu0 J_ext / 4 (so that Dpp = X g)
     float3 Dpp;  // eps_r E = D (physical displacement, eps0 = 1)
     float3 E;
     float3 B;
@@ -98,9 +99,10 @@ __device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0
     MMFields o;
     const float g = mat.c0.z;  // 1 / (1 + mu0 sigma / (4 eps_r))
     const float er = mat.c0.x, inv_er = mat.c0.y, sigma = mat.c1.x;
-    o.Dpp.x = (0.5f * dx - 0.5f * jext.x) * g;
-    o.Dpp.y = (0.5f * dy - 0.5f * jext.y) * g;
-    o.Dpp.z = (0.5f * dz - 0.5f * jext.z) * g;
+    o.X = make_float3(0.5f * dx - 0.5f * jext.x, 0.5f * dy - 0.5f * jext.y, 0.5f * dz - 0.5f * jext.z);
+    o.Dpp.x = o.X.x * g;
+    o.Dpp.y = o.X.y * g;
+    o.Dpp.z = o.X.z * g;
     o.E.x = div_rn(o.Dpp.x, er, inv_er);
     o.E.y = div_rn(o.Dpp.y, er, inv_er);
     o.E.z = div_rn(o.Dpp.z, er, inv_er);
@@ -134,7 +136,7 @@ __device__ __forceinline__ void mm_put(const StepArgs& a, int d, int i, float4 v
 }
 
 // Update of cell i; m is its index in the special-cell list when kSpecial.
-template <int S, int M, bool kSpecial, bool kRho>
+template <int S, int M, bool kSpecial, bool kRho, bool kRecord = false>
 __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m) {
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 f[12];
@@ -175,6 +177,15 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m) {
         mm_put<S>(a, d, i, o);
     });
     if constexpr (kRho) a.rho_out[i] = 2.f * F.rho - rest0;  // f_0^(0)eq = rho_c; stays in place
+    if constexpr (kRecord) {  // what the adjoint of this step needs: E and X
+        const int n = a.g.n;
+        a.rec[i] = F.E.x;
+        a.rec[n + i] = F.E.y;
+        a.rec[2 * n + i] = F.E.z;
+        a.rec[3 * n + i] = F.X.x;
+        a.rec[4 * n + i] = F.X.y;
+        a.rec[5 * n + i] = F.X.z;
+    }
 }
 
 template <int S, int M, bool kSpecial, bool kRho>
@@ -377,6 +388,158 @@ __global__ void __launch_bounds__(kBlock) mm_batch_special_kernel(const BatchLat
     }
 }
 
+template <int M, bool kSpecial, bool kRho>
+__global__ void __launch_bounds__(kBlock, 3) mm_record_kernel(StepArgs a) {
+    if constexpr (kSpecial) {
+        const int m = blockIdx.x * blockDim.x + threadIdx.x;
+        if (m >= a.sv.n_special) return;
+        mm_update<kF32, M, true, kRho, true>(a, a.sv.cell[m], m);
+    } else {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.g.n) return;
+        mm_update<kF32, M, false, kRho, true>(a, i, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint of one MM step. With per-velocity adjoints (a0^, a1^, c0^, c1^) of the post-collision
+// values, the transpose of eq. CollisionMiller through eq. equilibriumsMiller is
+//   adjoint of 2s_d = a0^ + a1^ + c0^ + c1^,  of 2 alpha_d = a0^ - a1^,  of 2 beta_d = c0^ - c1^,
+//   gJ = sum_d (2s_d)^ v_d / 8,   gE = sum_d (2 beta_d)^ e_d / 2 + sigma gJ   (e_d = e_{d0}, e_h = 2 e_d),
+//   gB = sum_d [(2 alpha_d)^ / (4 mu_r) + (2 beta_d)^ / 4] b_d,
+//   gDpp = sum_d (2 alpha_d)^ e_d / 2 + gE / eps_r   (E = Dpp / eps_r),   gX = g gDpp   (Dpp = X g),
+//   D' = sum_d (f_d0 - f_d1) e_d  ->  nu(f_d0) = e_d . gX - a0^,  nu(f_d1) = -e_d . gX - a1^,
+//   B  = sum_d (f'_d0 - f'_d1) b_d ->  nu(c0) = b_d . gB - c0^,  nu(c1) = -b_d . gB - c1^,
+// and the parameter derivatives (g = 1 / (1 + mu0 sigma / (4 eps_r)), mu0 = 2):
+//   dL/d eps_r += -gE . E / eps_r + gDpp . X * g^2 sigma / (2 eps_r^2),
+//   dL/d sigma += gJ . E - gDpp . X * g^2 / (2 eps_r).
+// Imposed cells output f_eq(E_imp, B_imp, 0): nothing flows back to f, and
+// d alpha_d / d eps_r = e_h . E_imp / 8. The plane loss |E|^2 adds 2E to gE.
+template <int M, bool kSpecial, bool kTerminal>
+__device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int m) {
+    const StepArgs& a = A.a;
+    const int n = a.g.n;
+    const Neighbourhood h = neighbourhood(a.g, i);
+    const MatCoef mat = load_coef<kModelMM, M>(a.media, i, a.eps0, a.mu0);
+    CellSource cs;
+    bool imposed = false;
+    if constexpr (kSpecial) {
+        cs = cell_source(a.sv, a.sc, m);
+        imposed = cs.imposed;
+    }
+    // Every load is issued up front: the source-cell mask of the main launch only gates the stores,
+    // so it adds no round trip before the others.
+    const bool skip = !kSpecial && !kTerminal && A.special_mask[i] != 0;
+    const float geps_old = __ldg(&A.grad_eps[i]), gsig_old = __ldg(&A.grad_sigma[i]);
+    // E and X of f^n: from the forward step's record, or (terminal) from the final state
+    float3 E, X;
+    if constexpr (kTerminal) {
+        float4 f[12];
+        mm_pull<kF32>(a, h, f);
+        const MMFields F = mm_fields<false>(f, 0.f, mat, make_float3(0.f, 0.f, 0.f));
+        E = F.E;
+        X = F.X;
+    } else {
+        E = make_float3(__ldg(&a.rec[i]), __ldg(&a.rec[n + i]), __ldg(&a.rec[2 * n + i]));
+        X = make_float3(__ldg(&a.rec[3 * n + i]), __ldg(&a.rec[4 * n + i]), __ldg(&a.rec[5 * n + i]));
+    }
+    struct {
+        float3 E, X;
+    } F{E, X};
+    const float inv_er = mat.c0.y, g = mat.c0.z, inv4mu = mat.c0.w, sigma = mat.c1.x;
+    float4 lam[12];
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        if constexpr (kTerminal) {
+            lam[d] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            const int dst = shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h);
+            lam[d] = __ldg(static_cast<const float4*>(A.nu_in) + (size_t)d * n + dst);
+        }
+    });
+    float gJx = 0.f, gJy = 0.f, gJz = 0.f, gAx = 0.f, gAy = 0.f, gAz = 0.f, gEx = 0.f, gEy = 0.f, gEz = 0.f;
+    float gBx = 0.f, gBy = 0.f, gBz = 0.f, geps_imposed = 0.f;
+    if (!imposed) {
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            const float s2 = (lam[d].x + lam[d].y) + (lam[d].z + lam[d].w);
+            const float a2 = lam[d].x - lam[d].y, b2 = lam[d].z - lam[d].w;
+            acc<kMMV[d][0]>(gJx, s2);
+            acc<kMMV[d][1]>(gJy, s2);
+            acc<kMMV[d][2]>(gJz, s2);
+            acc<kMMEh[d][0]>(gAx, a2);
+            acc<kMMEh[d][1]>(gAy, a2);
+            acc<kMMEh[d][2]>(gAz, a2);
+            acc<kMMEh[d][0]>(gEx, b2);
+            acc<kMMEh[d][1]>(gEy, b2);
+            acc<kMMEh[d][2]>(gEz, b2);
+            const float bcoef = __fmaf_rn(a2, inv4mu, 0.25f * b2);
+            acc<kMMB[d][0]>(gBx, bcoef);
+            acc<kMMB[d][1]>(gBy, bcoef);
+            acc<kMMB[d][2]>(gBz, bcoef);
+        });
+        gJx *= 0.125f; gJy *= 0.125f; gJz *= 0.125f;
+        gEx = __fmaf_rn(sigma, gJx, 0.25f * gEx);
+        gEy = __fmaf_rn(sigma, gJy, 0.25f * gEy);
+        gEz = __fmaf_rn(sigma, gJz, 0.25f * gEz);
+    } else if constexpr (kSpecial) {
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            const float ee = sdot<kMMEh[d][0], kMMEh[d][1], kMMEh[d][2]>(cs.E.x, cs.E.y, cs.E.z);
+            geps_imposed = __fmaf_rn(lam[d].x - lam[d].y, 0.125f * ee, geps_imposed);
+        });
+    }
+    if (A.loss_active && in_plane(h, a.g, A.plane_axis, A.plane_index)) {  // |E|^2 of time n
+        gEx = __fmaf_rn(2.f, F.E.x, gEx);
+        gEy = __fmaf_rn(2.f, F.E.y, gEy);
+        gEz = __fmaf_rn(2.f, F.E.z, gEz);
+        add_plane_loss<kTerminal>(A, h, F.E);
+    }
+    const float gDx = __fmaf_rn(gEx, inv_er, 0.25f * gAx), gDy = __fmaf_rn(gEy, inv_er, 0.25f * gAy),
+                gDz = __fmaf_rn(gEz, inv_er, 0.25f * gAz);
+    const float gXx = g * gDx, gXy = g * gDy, gXz = g * gDz;
+    if (skip) return;  // a source cell: the second launch writes it
+    float4* nu_out = static_cast<float4*>(A.nu_out);
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        const float gde = 0.5f * sdot<kMMEh[d][0], kMMEh[d][1], kMMEh[d][2]>(gXx, gXy, gXz);
+        const float gdb = sdot<kMMB[d][0], kMMB[d][1], kMMB[d][2]>(gBx, gBy, gBz);
+        float4 o;
+        if (imposed) o = make_float4(gde, -gde, gdb, -gdb);
+        else o = make_float4(gde - lam[d].x, -gde - lam[d].y, gdb - lam[d].z, -gdb - lam[d].w);
+        nu_out[(size_t)d * n + i] = o;
+    });
+    const float gEdotE = gEx * F.E.x + gEy * F.E.y + gEz * F.E.z;
+    const float gDdotX = gDx * F.X.x + gDy * F.X.y + gDz * F.X.z;
+    const float gg = g * g * inv_er;
+    float deps = geps_imposed - gEdotE * inv_er;
+    deps = __fmaf_rn(gDdotX, gg * 0.5f * sigma * inv_er, deps);
+    const float dsig = __fmaf_rn(-gDdotX, 0.5f * gg, gJx * F.E.x + gJy * F.E.y + gJz * F.E.z);
+    A.grad_eps[i] = geps_old + deps;
+    A.grad_sigma[i] = gsig_old + dsig;
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock, 3) mm_adjoint_kernel(AdjointArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.a.g.n) return;
+    mm_adjoint_cell<M, false, false>(A, i, 0);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock) mm_adjoint_special_kernel(AdjointArgs A) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= A.a.sv.n_special) return;
+    mm_adjoint_cell<M, true, false>(A, A.a.sv.cell[m], m);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kBlock) mm_adjoint_terminal_kernel(AdjointArgs A, int n_plane) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_plane) return;
+    mm_adjoint_cell<M, false, true>(A, plane_cell(A.a.g, A.plane_axis, A.plane_index, k), 0);
+}
+
 }  // namespace
 
 int mm_launch_step(const StepArgs& a, cudaStream_t st) {
@@ -498,6 +661,45 @@ int mm_batch_occupancy(int storage, int block, bool rho) {
                 &blocks, rho ? mm_batch_kernel<S, 256, true> : mm_batch_kernel<S, 256, false>, 256, 0);
     });
     return blocks;
+}
+
+int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st) {
+    int launched = 0;
+    with_media(A.a.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        mm_adjoint_kernel<M><<<blocks_for(A.a.g.n), kBlock, 0, st>>>(A);
+        launched = 1;
+        if (A.a.sv.n_special > 0) {
+            mm_adjoint_special_kernel<M><<<blocks_for(A.a.sv.n_special), kBlock, 0, st>>>(A);
+            launched = 2;
+        }
+    });
+    return launched;
+}
+
+int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st) {
+    with_media(A.a.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        mm_adjoint_terminal_kernel<M><<<blocks_for(n_plane), kBlock, 0, st>>>(A, n_plane);
+    });
+    return 1;
+}
+
+int mm_launch_record_step(const StepArgs& a, cudaStream_t st) {
+    int launched = 0;
+    const bool rho = a.rho_in != nullptr;
+    with_media(a.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        if (rho) mm_record_kernel<M, false, true><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+        else mm_record_kernel<M, false, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+        launched = 1;
+        if (a.sv.n_special > 0) {
+            if (rho) mm_record_kernel<M, true, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
+            else mm_record_kernel<M, true, false><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
+            launched = 2;
+        }
+    });
+    return launched;
 }
 
 }  // namespace lbm

@@ -91,6 +91,9 @@ def load_library(path: str | None = None):
         "lbm_last_error": (ctypes.c_char_p, [P]),
         "lbm_sync": (I, [P]),
         "lbm_destroy": (I, [P]),
+        "lbm_adjoint": (I, [P, I, I, I, I, ctypes.POINTER(D), P, P, I]),
+        "lbm_adjoint_release": (I, [P]),
+        "lbm_adjoint_workspace_bytes": (I64, [P]),
         "lbm_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
         "lbm_batch_step": (I, [P, ctypes.POINTER(I)]),
         "lbm_batch_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -268,6 +271,27 @@ class Lattice:
         self._check(self.lib.lbm_reduce(self.h, out))
         return float(out[0]), float(out[1]), float(out[2])
 
+    def adjoint(self, steps: int, plane_axis: int, plane_index: int, checkpoint_interval: int = 0):
+        """Advance `steps` steps and return (L, dL/d eps_r, dL/d sigma) for the plane loss
+        L = sum_t sum_plane |E(t)|^2 (lbm_adjoint); gradients are torch CUDA tensors (n,).
+        checkpoint_interval: < 0 keeps every step's record on the device, > 0 checkpoints the state
+        that often, 0 picks the first when it fits in half the free memory, else sqrt(steps)."""
+        import torch
+        ge = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        gs = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        loss = ctypes.c_double()
+        self._check(self.lib.lbm_adjoint(self.h, int(steps), int(plane_axis), int(plane_index), int(checkpoint_interval),
+                                         ctypes.byref(loss), ge.data_ptr(), gs.data_ptr(), 1))
+        return loss.value, ge, gs
+
+    def adjoint_release(self) -> None:
+        """Free the work space that adjoint() keeps between calls (lbm_adjoint_release)."""
+        self._check(self.lib.lbm_adjoint_release(self.h))
+
+    @property
+    def adjoint_workspace_bytes(self) -> int:
+        return int(self.lib.lbm_adjoint_workspace_bytes(self.h))
+
     def check_finite(self) -> bool:
         rc = self.lib.lbm_check_finite(self.h)
         if rc == -4:
@@ -337,3 +361,35 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def plane_loss(model: str, shape, eps_r, sigma=None, *, populations=None, sources=(), steps: int, plane_axis: int,
+               plane_index: int, t0: int = 0, checkpoint_interval: int = 0):
+    """L = sum_{t=1..steps} sum over plane (plane_axis, plane_index) of |E(t)|^2, differentiable in
+    eps_r (and sigma) with torch autograd. The gradient comes from the library's adjoint
+    (lbm_adjoint), computed when the loss is evaluated. eps_r and sigma are per-cell CUDA tensors;
+    the run starts from `populations` (canonical layout, default zero) at time t0."""
+    import torch
+
+    class _PlaneLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, eps, sig):
+            L = Lattice(model, shape, eps_r=eps.detach(), sigma=None if sig is None else sig.detach())
+            for s in sources:
+                L.add_source(s)
+            q = 50 if model == "mm" else 36
+            f0 = populations if populations is not None else torch.zeros((q, L.n), device=eps.device)
+            L.set_populations(f0, t0)
+            loss, ge, gs = L.adjoint(steps, plane_axis, plane_index, checkpoint_interval)
+            ctx.save_for_backward(ge, gs)
+            ctx.has_sigma = sig is not None
+            L.close()
+            return torch.tensor(loss, dtype=torch.float64, device=eps.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            ge, gs = ctx.saved_tensors
+            g = grad_out.to(torch.float32)
+            return g * ge, (g * gs if ctx.has_sigma else None)
+
+    return _PlaneLoss.apply(eps_r, sigma)

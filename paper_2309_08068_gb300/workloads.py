@@ -144,11 +144,13 @@ def dipole_cells(shape, center, alpha: float = 0.5, r2_max: float = 36.0):
     return cells, W
 
 
-def hertz_dipole(model: str, n: int = 256, period: float = 32.0, j0: float = 1e-4, steps: int = 2000) -> Workload:
+def hertz_dipole(model: str, n: int = 256, period: float = 32.0, j0: float = 1e-4, steps: int = 2000,
+                 r2_max: float = 36.0) -> Workload:
     """Hertz dipole in an n^3 vacuum lattice (Section IV-C source at the benchmark's size): current
-    J0 exp(-0.5 |x - x_d|^2) sin(2 pi t / period) z at the centre cell, zero initial fields."""
+    J0 exp(-0.5 |x - x_d|^2) sin(2 pi t / period) z at the centre cell, truncated at |x - x_d|^2 <=
+    r2_max, zero initial fields."""
     shape = (n, n, n)
-    cells, W = dipole_cells(shape, (n // 2, n // 2, n // 2))
+    cells, W = dipole_cells(shape, (n // 2, n // 2, n // 2), r2_max=r2_max)
     src = Source("current", cells, TimeFunction("sin", j0, period, 0.0), w=W)
     return Workload("hertz_dipole", model, shape, steps, sources=[src])
 
@@ -204,12 +206,12 @@ def refinement_batch(model: str, sigma: float, sizes=REFINEMENT_SIZES) -> list:
 
 
 def random_medium_dipole(model: str, n: int = 128, seed: int = 5, period: float = 24.0, j0: float = 1e-4,
-                         steps: int = 1000) -> Workload:
+                         steps: int = 1000, r2_max: float = 36.0) -> Workload:
     """Dipole (as ``hertz_dipole``, period 24) in an n^3 lattice whose eps_r is uniform in [1, 4) per
     cell from numpy's default_rng(seed)."""
     rng = np.random.default_rng(seed)
     eps = rng.uniform(1.0, 4.0, n * n * n)
-    w = hertz_dipole(model, n, period, j0, steps)
+    w = hertz_dipole(model, n, period, j0, steps, r2_max=r2_max)
     w.name = "random_medium_dipole"
     w.eps_r = eps
     return w

@@ -1,0 +1,174 @@
+"""GPU adjoint (lbm_adjoint): loss and dL/d eps_r, dL/d sigma against the FP64 oracle's adjoint and
+its central finite differences.
+
+Tolerance from the arithmetic. The loss is the FP32 forward path, so relative error is at most 1e-5.
+The gradients add one FP32 rounding per backward step and per term to that path's error. Over T <= 100
+steps they stay well inside 1e-4 relative L2, and the tests require that.
+"""
+import numpy as np
+import pytest
+
+from helpers import oracle_from_workload, rel_l2
+from paper_2309_08068_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+GRAD_TOL = 1e-4
+LOSS_TOL = 1e-5
+
+
+def f32(a):
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
+def small_case(model, seed=81, shape=(8, 7, 6), plane=(0, 5)):
+    """Per-cell eps_r and sigma, a current source and an imposed source away from the plane."""
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(shape))
+    nx, ny, nz = shape
+    eps = f32(rng.uniform(1.0, 3.0, n))
+    sig = f32(rng.uniform(0.0, 0.3, n) * (rng.random(n) < 0.5))
+    cur = np.array([2 + nx * (3 + ny * 2), 1 + nx * (4 + ny * 3)], dtype=np.int64)
+    imp = np.array([3 + nx * (1 + ny * 4)], dtype=np.int64)
+    sources = [wl.Source("current", cur, wl.TimeFunction("sin", 1.0, 9.0, 0.4), w=f32(rng.standard_normal((2, 3)))),
+               wl.Source("impose", imp, wl.TimeFunction("sin", 0.5, 11.0, 0.1),
+                         E0=tuple(f32(rng.standard_normal(3))), B0=tuple(f32(rng.standard_normal(3))))]
+    f0 = f32(0.1 * rng.standard_normal((wl.POPULATIONS[model], n)))
+    w = wl.Workload("adj", model, shape, 0, eps_r=eps, sigma=sig, sources=sources)
+    return w, f0, plane
+
+
+def gpu_adjoint(w, f0, steps, plane, interval=0, t0=3):
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    L = lattice_from_workload(w, init=False)
+    L.set_populations(np.asarray(f0, np.float32), t0)
+    loss, ge, gs = L.adjoint(steps, plane[0], plane[1], interval)
+    return L, loss, ge.cpu().numpy(), gs.cpu().numpy()
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_adjoint_matches_oracle_adjoint(model):
+    w, f0, plane = small_case(model)
+    steps = 20
+    L, loss, ge, gs = gpu_adjoint(w, f0, steps, plane, interval=6)  # segments 6, 6, 6, 2
+    O = oracle_from_workload(w, init=False, threads=8)
+    O.set_populations(f0, 3)
+    loss_ref, ge_ref, gs_ref = O.loss_and_gradient(steps, *plane)
+    assert abs(loss - loss_ref) <= LOSS_TOL * loss_ref
+    assert rel_l2(ge, ge_ref) <= GRAD_TOL, rel_l2(ge, ge_ref)
+    assert rel_l2(gs, gs_ref) <= GRAD_TOL, rel_l2(gs, gs_ref)
+    # the context advanced exactly like lbm_step
+    assert L.time == 3 + steps
+    assert rel_l2(L.populations_host()[:48 if model == "mm" else 36], O.populations()[:48 if model == "mm" else 36]) <= 1e-5
+    print(f"adjoint {model}: loss rel {abs(loss - loss_ref) / loss_ref:.2e}, grad eps rel L2 "
+          f"{rel_l2(ge, ge_ref):.2e}, grad sigma rel L2 {rel_l2(gs, gs_ref):.2e}")
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_checkpoint_interval_does_not_change_the_result(model):
+    """Recomputation replays the same kernels on the same states: every checkpoint interval, and
+    keeping every step's record resident (interval -1), gives the same loss and gradients bit for bit."""
+    w, f0, plane = small_case(model, seed=82)
+    results = [gpu_adjoint(w, f0, 17, plane, interval=k)[1:] for k in (1, 3, 0, 17, -1)]
+    for loss, ge, gs in results[1:]:
+        assert loss == results[0][0]
+        assert np.array_equal(ge, results[0][1])
+        assert np.array_equal(gs, results[0][2])
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_autograd_plane_loss(model):
+    from paper_2309_08068_gb300.lbm import plane_loss
+    w, f0, plane = small_case(model, seed=83)
+    eps = torch.tensor(w.eps_r, dtype=torch.float32, device="cuda", requires_grad=True)
+    sig = torch.tensor(w.sigma, dtype=torch.float32, device="cuda", requires_grad=True)
+    pops = torch.tensor(np.asarray(f0, np.float32), device="cuda")
+    loss = plane_loss(model, w.shape, eps, sig, populations=pops, sources=w.sources, steps=12,
+                      plane_axis=plane[0], plane_index=plane[1], t0=3)
+    (3.0 * loss).backward()
+    _, loss2, ge, gs = gpu_adjoint(w, f0, 12, plane)
+    assert loss.item() == loss2
+    assert np.allclose(eps.grad.cpu().numpy(), 3.0 * ge, rtol=1e-6, atol=0)
+    assert np.allclose(sig.grad.cpu().numpy(), 3.0 * gs, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_random_medium_dipole_gradient_16cube(model):
+    """The inverse-design check at its stated size: 16^3, per-cell eps_r in [1, 4), dipole at
+    (8, 8, 8) with period 24, T = 100 steps, plane x = 12. GPU adjoint against the FP64 oracle adjoint
+    over the whole lattice, and against oracle central differences at a few cells. The dipole is
+    truncated at radius 3 so that no source cell lies in the plane."""
+    w = wl.random_medium_dipole(model, n=16, seed=5, period=24.0, steps=100, r2_max=9.0)
+    w.eps_r = f32(w.eps_r)
+    for s in w.sources:
+        s.w = f32(s.w)
+    plane = (0, 12)
+    q = wl.POPULATIONS[model]
+    f0 = np.zeros((q, w.n))
+    _, loss, ge, _ = gpu_adjoint(w, f0, w.steps, plane, t0=0)
+    O = oracle_from_workload(w, init=False, threads=8)
+    O.set_populations(f0, 0)
+    loss_ref, ge_ref, _ = O.loss_and_gradient(w.steps, *plane)
+    assert abs(loss - loss_ref) <= LOSS_TOL * loss_ref
+    assert rel_l2(ge, ge_ref) <= GRAD_TOL, rel_l2(ge, ge_ref)
+    for c in (8 + 16 * (8 + 16 * 8) + 2, 11 + 16 * (3 + 16 * 9), 12 + 16 * (8 + 16 * 8)):
+        vals = []
+        for sgn in (1, -1):
+            eps = w.eps_r.copy()
+            h = 1e-5 * eps[c]
+            eps[c] += sgn * h
+            w2 = wl.Workload(w.name, model, w.shape, 0, eps_r=eps, sources=w.sources)
+            O2 = oracle_from_workload(w2, init=False, threads=8)
+            O2.set_populations(f0, 0)
+            total = 0.0
+            for t in range(1, w.steps + 1):
+                O2.step(1)
+                total += O2.plane_loss(t, O2.populations(), *plane)
+            vals.append(total)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(ge[c] - fd) <= GRAD_TOL * np.abs(ge_ref).max(), (c, ge[c], fd)
+    print(f"16^3 dipole {model}: loss {loss:.6e} (oracle {loss_ref:.6e}), grad rel L2 {rel_l2(ge, ge_ref):.2e}")
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("plane", [(1, 2), (2, 1)])
+def test_loss_planes_on_other_axes(model, plane):
+    """Planes of constant y and constant z (the loss slots of each orientation), against the oracle."""
+    w, f0, _ = small_case(model, seed=85)
+    steps = 9
+    _, loss, ge, gs = gpu_adjoint(w, f0, steps, plane)
+    O = oracle_from_workload(w, init=False, threads=8)
+    O.set_populations(f0, 3)
+    loss_ref, ge_ref, gs_ref = O.loss_and_gradient(steps, *plane)
+    assert abs(loss - loss_ref) <= LOSS_TOL * loss_ref
+    assert rel_l2(ge, ge_ref) <= GRAD_TOL, rel_l2(ge, ge_ref)
+    assert rel_l2(gs, gs_ref) <= GRAD_TOL, rel_l2(gs, gs_ref)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_workspace_is_kept_grown_and_released(model):
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    w, f0, plane = small_case(model, seed=86)
+    L = lattice_from_workload(w, init=False)
+
+    def run(steps, interval=0):
+        L.set_populations(np.asarray(f0, np.float32), 3)
+        loss, ge, gs = L.adjoint(steps, *plane, interval)
+        return loss, ge.cpu().numpy(), gs.cpu().numpy()
+
+    assert L.adjoint_workspace_bytes == 0
+    first = run(10)
+    held = L.adjoint_workspace_bytes
+    assert held > 0
+    again = run(10)
+    assert L.adjoint_workspace_bytes == held
+    run(30)
+    assert L.adjoint_workspace_bytes > held
+    L.adjoint_release()
+    assert L.adjoint_workspace_bytes == 0
+    last = run(10)
+    for r in (again, last):
+        assert r[0] == first[0]
+        assert np.array_equal(r[1], first[1]) and np.array_equal(r[2], first[2])
