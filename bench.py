@@ -255,6 +255,50 @@ def refinement_sweep(stream, steps: int):
     return out
 
 
+def slab_decomposition(stream, n: int, steps: int):
+    """The n^3 dipole lattice split into 2 and 4 z-slabs on this one GPU, each slab with two ghost
+    planes and one halo exchange per interface before every step, against the unsplit lattice:
+    `steps` steps each, CUDA events on the lattices' stream. What a multi-GPU slab run adds per GPU,
+    apart from moving the packed faces between devices."""
+    import torch
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    from paper_2309_08068_gb300.slabs import Slabs
+    out = {}
+    for model in ("mm", "hv"):
+        w = wl.hertz_dipole(model, n=n, steps=steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            L = lattice_from_workload(w, stream=stream)
+        L.step(3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_one = e0.elapsed_time(e1) / steps
+        halo = None
+        L.close()
+        res = {"unsplit_ms_per_step": round(ms_one, 4)}
+        for parts in (2, 4):
+            with torch.cuda.stream(stream):
+                S = Slabs(w, parts, stream=stream)
+            S.step(3)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            S.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            halo = S.lattices[0].halo_bytes
+            res[f"slabs_{parts}"] = {"ms_per_step": round(ms, 4), "over_unsplit": round(ms / ms_one, 4),
+                                     "MLUPS": round(w.n / (ms * 1e-3) / 1e6, 1)}
+            S.close()
+            torch.cuda.empty_cache()
+        res["halo_bytes_per_face"] = halo
+        out[model] = res
+    return out
+
+
 def adjoint_cost(stream, steps: int):
     """Inverse-design workload: 128^3 lattice, per-cell eps_r uniform in [1, 4), dipole with period
     24, loss plane x = 100. Time `steps` forward steps, then lbm_adjoint over `steps` steps from the
@@ -303,6 +347,19 @@ def adjoint_cost(stream, steps: int):
             torch.cuda.empty_cache()
         res["loss"] = losses[0]
         res["modes_agree"] = losses[0] == losses[1]
+        # Field energy every steps/4 steps: both schemes grow exponentially on this random medium,
+        # which bounds how far the gradient is meaningful.
+        with torch.cuda.stream(stream):
+            L = lattice_from_workload(w, stream=stream)
+        energy = {}
+        for k in range(1, 5):
+            L.step(steps // 4)
+            energy[str(k * (steps // 4))] = L.reduce()[0]
+        L.close()
+        res["field_energy"] = energy
+        e_half, e_end = energy[str(2 * (steps // 4))], energy[str(4 * (steps // 4))]
+        res["energy_growth_per_step"] = (math.log(e_end / e_half) / (steps - 2 * (steps // 4))
+                                         if e_half > 0 and e_end > 0 else None)
         out[model] = res
     return out
 
@@ -426,6 +483,7 @@ def run_ours(args):
     accuracy = storage_accuracy() if rank == 0 else None
     refinement = refinement_sweep(stream, args.refine_steps) if args.refine_steps > 0 else None
     adjoint = adjoint_cost(stream, args.adjoint_steps) if args.adjoint_steps > 0 else None
+    slabs = slab_decomposition(stream, args.n, args.slab_steps) if args.slab_steps > 0 else None
 
     # end to end through the C ABI with host buffers: upload fields, K steps, read E and B back
     pinned_E = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
@@ -495,6 +553,7 @@ def run_ours(args):
         "rel_l2_vs_fp64_dielectric_pulse_1500": accuracy,
         "refinement_batch": refinement,
         "adjoint": adjoint,
+        "slab_decomposition_one_gpu": slabs,
         "gpu_launches": int(launches),
         "finite": finite,
         "clocks": clocks.summary(),
@@ -513,6 +572,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--slab-steps", type=int, default=50,
+                    help="steps of the z-slab decomposition measurement on the dipole lattice (0 skips it)")
     ap.add_argument("--adjoint-steps", type=int, default=1000,
                     help="steps of the adjoint-cost measurement on the 128^3 random medium (0 skips it)")
     ap.add_argument("--refine-steps", type=int, default=100,

@@ -69,7 +69,15 @@ typedef struct {
  *   populations are not stored (neither enters E, B, D, H or J) and read back as 0.
  * eps0, mu0: vacuum constants; 0 selects the model default. MM fixes eps0 = 1, mu0 = 2 (Section
  *   II-A; any other value gives LBM_EUNSUPPORTED). HV default eps0 = mu0 = 3: the paper fixes only
- *   the vacuum speed 1/sqrt(eps0 mu0) = 1/3 (Section III-A), which the split does not change. */
+ *   the vacuum speed 1/sqrt(eps0 mu0) = 1/3 (Section III-A), which the split does not change.
+ * z_ghost: 1 makes the context one z-slab of a larger lattice (nz >= 3). Planes z = 0 and z = nz - 1
+ *   are ghost planes holding the neighbouring slabs' populations: lbm_step updates only the planes
+ *   1 .. nz - 2, lbm_reduce and lbm_check_finite sum only those, and sources may not lie in a ghost
+ *   plane. Before every step the ghost planes must receive the neighbours' halo (lbm_halo_unpack
+ *   or lbm_halo_exchange). A cell's populations are read from its neighbours (pull scheme), so
+ *   lbm_fields, lbm_get_populations and lbm_reduce of the boundary planes also need a current halo:
+ *   exchange after the last step before reading. The other values of the ghost planes are
+ *   unspecified. Not accepted by lbm_batch_create or lbm_adjoint. */
 typedef struct {
     int storage;
     void* cuda_stream;
@@ -77,6 +85,7 @@ typedef struct {
     double eps0;
     double mu0;
     double storage_scale;
+    int z_ghost;
 } lbm_options;
 
 /* Time dependence s(t) of a source, evaluated on the host in double precision for iteration t.
@@ -224,6 +233,36 @@ int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_index, int ch
 int lbm_adjoint_release(lbm_ctx* ctx);
 /* Bytes of device memory held as lbm_adjoint work space (0 when none; -1 for NULL). */
 int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------------
+ * z-slab decomposition. The scheme couples a cell only to its 3 x 3 x 3 neighbourhood (Sections II
+ * and III, advection), so a lattice can be split into slabs along z that exchange one plane of
+ * populations per face and step. A slab context (z_ghost = 1) has one ghost plane at each end. After
+ * a step, the values that leave a slab through a face are the post-collision populations of its
+ * boundary plane in the directions that cross that face. The pull scheme stores them at the cell
+ * that produced them, so they are copied unchanged into the neighbour's ghost plane:
+ *   face 1 (up): plane nz - 2, directions with v_z = +1 (MM groups 4, 5, 8, 9; HV direction +z),
+ *     which the upper neighbour reads from its plane 0;
+ *   face 0 (down): plane 1, directions with v_z = -1 (MM groups 6, 7, 10, 11; HV direction -z),
+ *     which the lower neighbour reads from its plane nz - 1.
+ * A packed face is those directions' planes one after another, each nx * ny cells in the context's
+ * storage layout: MM 4 x 16 B per cell in FP32 (8 B in 16-bit storage); HV 16 B + 8 B (8 B + 4 B).
+ * MM's rest populations do not move and are not exchanged. Slabs stepped this way give the same
+ * populations, bit for bit, as the unsplit lattice.
+ * ------------------------------------------------------------------------------------------- */
+/* Bytes of one packed face (z_ghost contexts; LBM_EINVAL otherwise, as a negative value). */
+int64_t lbm_halo_bytes(const lbm_ctx* ctx);
+/* Pack the outgoing values of face 0 or 1 of the current state into dst (lbm_halo_bytes bytes;
+ * device memory when on_device, else host memory and the call waits for the stream). */
+int lbm_halo_pack(lbm_ctx* ctx, int face, void* dst, int on_device);
+/* Write a face packed by the neighbour into ghost plane 0 (face 0: the lower neighbour's face 1) or
+ * nz - 1 (face 1: the upper neighbour's face 0) of the current state. */
+int lbm_halo_unpack(lbm_ctx* ctx, int face, const void* src, int on_device);
+/* Both directions across the interface between `lower` (whose face 1 it is) and `upper` (face 0),
+ * on one device, in one kernel: lower's face 1 into upper's plane 0, upper's face 0 into lower's
+ * plane nz - 1. The contexts must have the same model, storage, nx, ny, device and stream;
+ * lower == upper closes a single slab periodically. Stream-ordered. */
+int lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper);
 
 /* ---------------------------------------------------------------------------------------------
  * Batched stepping of lattices of uneven sizes. The paper's studies are mesh-refinement sweeps:

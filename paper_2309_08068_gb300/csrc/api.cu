@@ -39,6 +39,7 @@ struct lbm_ctx {
     Geometry g{};
     cudaStream_t stream = nullptr;
     int track_rho = 0;
+    int z_ghost = 0;  // z-slab with ghost planes 0 and nz - 1 (stepped planes 1 .. nz - 2)
     double eps0 = 0, mu0 = 0;
     int device = 0;
     int storage = LBM_F32;
@@ -73,6 +74,9 @@ struct lbm_ctx {
     // adjoint work space (records, checkpoints, adjoint states), kept between lbm_adjoint calls
     void* adj_ws = nullptr;
     size_t adj_ws_bytes = 0;
+    // staging of a packed halo face for host-side lbm_halo_pack / lbm_halo_unpack
+    void* halo_stage = nullptr;
+    size_t halo_stage_bytes = 0;
     int64_t t = 0;
     int64_t launches = 0;
     std::string err;
@@ -124,6 +128,8 @@ StepArgs base_args(lbm_ctx* c) {
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.g = c->g;
+    a.cell_begin = c->z_ghost ? c->g.nx * c->g.ny : 0;
+    a.cell_end = c->z_ghost ? c->g.n - c->g.nx * c->g.ny : c->g.n;
     a.media_mode = c->media_mode;
     a.media.uniform = c->uniform;
     a.media.id = c->mat_id;
@@ -375,6 +381,8 @@ void release(lbm_ctx* c) {
     free_dev(c->d_result);
     free_dev(c->adj_ws);
     c->adj_ws_bytes = 0;
+    free_dev(c->halo_stage);
+    c->halo_stage_bytes = 0;
 }
 
 // Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
@@ -415,6 +423,9 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
     if (!(scale > 0) || !std::isfinite(scale) || std::frexp(scale, &scale_exp) != 0.5 || scale_exp < -100 ||
         scale_exp > 100)
         return fail(nullptr, LBM_EINVAL, "lbm_create: storage_scale must be a power of two in [2^-100, 2^100]");
+    const int z_ghost = opts ? opts->z_ghost : 0;
+    if (z_ghost != 0 && z_ghost != 1) return fail(nullptr, LBM_EINVAL, "lbm_create: z_ghost must be 0 or 1");
+    if (z_ghost && nz < 3) return fail(nullptr, LBM_EINVAL, "lbm_create: a z_ghost slab needs nz >= 3");
     double eps0 = opts ? opts->eps0 : 0.0, mu0 = opts ? opts->mu0 : 0.0;
     if (eps0 < 0 || mu0 < 0 || !std::isfinite(eps0) || !std::isfinite(mu0))
         return fail(nullptr, LBM_EINVAL, "lbm_create: eps0, mu0 must be >= 0");
@@ -435,6 +446,7 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
     magic_for(nx * ny, &c->g.mxy, &c->g.kxy);
     c->stream = opts ? static_cast<cudaStream_t>(opts->cuda_stream) : nullptr;
     c->track_rho = (opts && opts->track_rho && model == LBM_MM) ? 1 : 0;
+    c->z_ghost = z_ghost;
     c->eps0 = eps0;
     c->mu0 = mu0;
     c->storage = storage;
@@ -560,6 +572,9 @@ int lbm_set_source(lbm_ctx* ctx, const lbm_source* src) {
     for (int64_t m = 0; m < src->n_cells; ++m) {
         if (src->cells[m] < 0 || src->cells[m] >= ctx->g.n)
             return fail(ctx, LBM_EINVAL, "lbm_set_source: cell %lld out of range", (long long)src->cells[m]);
+        const int64_t plane = src->cells[m] / ((int64_t)ctx->g.nx * ctx->g.ny);
+        if (ctx->z_ghost && (plane == 0 || plane == ctx->g.nz - 1))
+            return fail(ctx, LBM_EINVAL, "lbm_set_source: cell %lld lies in a ghost plane", (long long)src->cells[m]);
         s.cells[(size_t)m] = (int)src->cells[m];
     }
     if (src->kind == LBM_SRC_CURRENT) s.w.assign(src->w, src->w + 3 * src->n_cells);
@@ -767,6 +782,41 @@ __global__ void __launch_bounds__(kBlock) sum_doubles_kernel(const double* __res
 
 int launch_sum_doubles(const double* v, int count, double* result, cudaStream_t st) {
     sum_doubles_kernel<<<1, kBlock, 0, st>>>(v, count, result);
+    return 1;
+}
+
+namespace {
+// blockIdx.y selects the chunk; blocks stride over its words. W is the widest of 16, 8, 4 bytes that
+// divides both addresses and the size (decided on the host, the same for every block of a chunk).
+template <typename W>
+__device__ __forceinline__ void copy_words(const HaloChunk& c) {
+    const W* __restrict__ src = reinterpret_cast<const W*>(c.src);
+    W* __restrict__ dst = reinterpret_cast<W*>(c.dst);
+    const long long words = c.bytes / (long long)sizeof(W);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < words;
+         k += (long long)gridDim.x * blockDim.x)
+        dst[k] = src[k];
+}
+
+__global__ void __launch_bounds__(kBlock) halo_copy_kernel(HaloCopy h) {
+    const HaloChunk& c = h.c[blockIdx.y];
+    if (c.width == 16) copy_words<uint4>(c);
+    else if (c.width == 8) copy_words<uint2>(c);
+    else copy_words<unsigned>(c);
+}
+}  // namespace
+
+int launch_halo_copy(HaloCopy h, cudaStream_t st) {
+    if (h.count <= 0) return 0;
+    long long most = 0;
+    for (int k = 0; k < h.count; ++k) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(h.c[k].src) | reinterpret_cast<uintptr_t>(h.c[k].dst) |
+                            (uintptr_t)h.c[k].bytes;
+        h.c[k].width = (a % 16 == 0) ? 16 : (a % 8 == 0 ? 8 : 4);
+        most = std::max(most, h.c[k].bytes / h.c[k].width);
+    }
+    const int bx = (int)std::max<long long>(1, std::min<long long>((most + kBlock - 1) / kBlock, 152 * 4));
+    halo_copy_kernel<<<dim3(bx, h.count), kBlock, 0, st>>>(h);
     return 1;
 }
 }  // namespace lbm
@@ -1031,6 +1081,8 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out) {
     if (!ctxs || count < 1) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: need at least one context");
     for (int k = 0; k < count; ++k) {
         if (!ctxs[k]) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d is NULL", k);
+        if (ctxs[k]->z_ghost)
+            return bfail(nullptr, LBM_EUNSUPPORTED, "lbm_batch_create: context %d is a z_ghost slab", k);
         for (int q = 0; q < k; ++q)
             if (ctxs[q] == ctxs[k]) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d repeated", k);
         if (ctxs[k]->model != ctxs[0]->model || ctxs[k]->storage != ctxs[0]->storage ||
@@ -1228,6 +1280,7 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
     if (steps < 1) return fail(ctx, LBM_EINVAL, "lbm_adjoint: steps must be >= 1");
     if (!loss_out) return fail(ctx, LBM_EINVAL, "lbm_adjoint: loss_out is NULL");
     if (ctx->storage != LBM_F32) return fail(ctx, LBM_EUNSUPPORTED, "lbm_adjoint: needs FP32 population storage");
+    if (ctx->z_ghost) return fail(ctx, LBM_EUNSUPPORTED, "lbm_adjoint: not available on a z_ghost slab");
     const int dims[3] = {ctx->g.nx, ctx->g.ny, ctx->g.nz};
     if (plane_axis < 0 || plane_axis > 2 || plane_index < 0 || plane_index >= dims[plane_axis])
         return fail(ctx, LBM_EINVAL, "lbm_adjoint: plane (axis %d, index %d) outside the lattice", plane_axis,
@@ -1416,3 +1469,148 @@ extern "C" int lbm_adjoint_release(lbm_ctx* ctx) {
 }
 
 extern "C" int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx) { return ctx ? (int64_t)ctx->adj_ws_bytes : -1; }
+
+// ------------------------------------------------------------------------------------------------
+// z-slab halo: pack, unpack and exchange of the populations that cross a z face.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+// Device planes of one face's crossing directions: for each direction its group plane (and, for
+// HV, its pair plane). plane_z selects the plane; dirs are the directions crossing the face.
+struct FacePlanes {
+    int count = 0;
+    char* ptr[8];
+    size_t bytes[8];
+};
+
+FacePlanes face_planes(lbm_ctx* c, int plane_z, int vz_sign) {
+    FacePlanes f;
+    const size_t nxy = (size_t)c->g.nx * c->g.ny;
+    const size_t n = (size_t)c->g.n;
+    const size_t g_elem = group_bytes(c->model, c->storage) / (c->model == LBM_MM ? 12 : 6);
+    int dirs[4];
+    const int nd = c->model == LBM_MM ? mm_halo_dirs(vz_sign, dirs) : hv_halo_dirs(vz_sign, dirs);
+    char* g = static_cast<char*>(c->buf[c->cur]);
+    for (int k = 0; k < nd; ++k) {
+        f.ptr[f.count] = g + g_elem * ((size_t)dirs[k] * n + (size_t)plane_z * nxy);
+        f.bytes[f.count++] = g_elem * nxy;
+    }
+    if (c->model == LBM_HV) {
+        const size_t p_elem = pair_bytes(c->storage) / 6;
+        char* p = static_cast<char*>(c->buf2[c->cur]);
+        for (int k = 0; k < nd; ++k) {
+            f.ptr[f.count] = p + p_elem * ((size_t)dirs[k] * n + (size_t)plane_z * nxy);
+            f.bytes[f.count++] = p_elem * nxy;
+        }
+    }
+    return f;
+}
+
+// Outgoing values of face 0 (plane 1, v_z = -1) or face 1 (plane nz - 2, v_z = +1).
+FacePlanes outgoing(lbm_ctx* c, int face) { return face == 0 ? face_planes(c, 1, -1) : face_planes(c, c->g.nz - 2, +1); }
+// Ghost planes written by face 0 (plane 0, v_z = +1) or face 1 (plane nz - 1, v_z = -1).
+FacePlanes incoming(lbm_ctx* c, int face) { return face == 0 ? face_planes(c, 0, +1) : face_planes(c, c->g.nz - 1, -1); }
+
+size_t face_bytes(const FacePlanes& f) {
+    size_t b = 0;
+    for (int k = 0; k < f.count; ++k) b += f.bytes[k];
+    return b;
+}
+
+int check_slab(lbm_ctx* c, const char* who) {
+    if (!c) return LBM_EINVAL;
+    if (!c->z_ghost) return fail(c, LBM_EINVAL, "%s: the context is not a z_ghost slab", who);
+    return ensure_device(c);
+}
+
+// Staging buffer for host-side pack/unpack (one face), allocated on first use.
+int halo_staging(lbm_ctx* c, size_t bytes, char** out) {
+    if (c->halo_stage_bytes < bytes) {
+        free_dev(c->halo_stage);
+        c->halo_stage_bytes = 0;
+        if (cudaMalloc(&c->halo_stage, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->halo_stage = nullptr;
+            return fail(c, LBM_ENOMEM, "halo: cannot allocate %zu bytes of staging", bytes);
+        }
+        c->halo_stage_bytes = bytes;
+    }
+    *out = static_cast<char*>(c->halo_stage);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t lbm_halo_bytes(const lbm_ctx* ctx) {
+    if (!ctx || !ctx->z_ghost) return LBM_EINVAL;
+    return (int64_t)face_bytes(outgoing(const_cast<lbm_ctx*>(ctx), 1));
+}
+
+extern "C" int lbm_halo_pack(lbm_ctx* ctx, int face, void* dst, int on_device) {
+    int rc;
+    if ((rc = check_slab(ctx, "lbm_halo_pack")) != LBM_OK) return rc;
+    if (face != 0 && face != 1) return fail(ctx, LBM_EINVAL, "lbm_halo_pack: face must be 0 or 1");
+    if (!dst) return fail(ctx, LBM_EINVAL, "lbm_halo_pack: dst is NULL");
+    const FacePlanes f = outgoing(ctx, face);
+    const size_t total = face_bytes(f);
+    char* d = static_cast<char*>(dst);
+    if (!on_device && (rc = halo_staging(ctx, total, &d)) != LBM_OK) return rc;
+    HaloCopy h;
+    memset(&h, 0, sizeof(h));
+    size_t off = 0;
+    for (int k = 0; k < f.count; ++k) {
+        h.c[h.count++] = HaloChunk{f.ptr[k], d + off, (long long)f.bytes[k]};
+        off += f.bytes[k];
+    }
+    if ((rc = check_launch(ctx, launch_halo_copy(h, ctx->stream))) != LBM_OK) return rc;
+    if (!on_device) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(dst, d, total, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_halo_unpack(lbm_ctx* ctx, int face, const void* src, int on_device) {
+    int rc;
+    if ((rc = check_slab(ctx, "lbm_halo_unpack")) != LBM_OK) return rc;
+    if (face != 0 && face != 1) return fail(ctx, LBM_EINVAL, "lbm_halo_unpack: face must be 0 or 1");
+    if (!src) return fail(ctx, LBM_EINVAL, "lbm_halo_unpack: src is NULL");
+    const FacePlanes f = incoming(ctx, face);
+    const size_t total = face_bytes(f);
+    const char* s = static_cast<const char*>(src);
+    if (!on_device) {
+        char* stage = nullptr;
+        if ((rc = halo_staging(ctx, total, &stage)) != LBM_OK) return rc;
+        CUDA_TRY(ctx, cudaMemcpyAsync(stage, src, total, cudaMemcpyHostToDevice, ctx->stream));
+        s = stage;
+    }
+    HaloCopy h;
+    memset(&h, 0, sizeof(h));
+    size_t off = 0;
+    for (int k = 0; k < f.count; ++k) {
+        h.c[h.count++] = HaloChunk{s + off, f.ptr[k], (long long)f.bytes[k]};
+        off += f.bytes[k];
+    }
+    if ((rc = check_launch(ctx, launch_halo_copy(h, ctx->stream))) != LBM_OK) return rc;
+    if (!on_device) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // the host source may be reused
+    return LBM_OK;
+}
+
+extern "C" int lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper) {
+    int rc;
+    if (!lower || !upper) return LBM_EINVAL;
+    if ((rc = check_slab(lower, "lbm_halo_exchange")) != LBM_OK) return rc;
+    if ((rc = check_slab(upper, "lbm_halo_exchange")) != LBM_OK) return rc;
+    if (lower->model != upper->model || lower->storage != upper->storage || lower->g.nx != upper->g.nx ||
+        lower->g.ny != upper->g.ny || lower->device != upper->device || lower->stream != upper->stream)
+        return fail(lower, LBM_EINVAL,
+                    "lbm_halo_exchange: slabs must share model, storage, nx, ny, device and stream");
+    const FacePlanes up_src = outgoing(lower, 1), up_dst = incoming(upper, 0);
+    const FacePlanes down_src = outgoing(upper, 0), down_dst = incoming(lower, 1);
+    HaloCopy h;
+    memset(&h, 0, sizeof(h));
+    for (int k = 0; k < up_src.count; ++k) h.c[h.count++] = HaloChunk{up_src.ptr[k], up_dst.ptr[k], (long long)up_src.bytes[k]};
+    for (int k = 0; k < down_src.count; ++k)
+        h.c[h.count++] = HaloChunk{down_src.ptr[k], down_dst.ptr[k], (long long)down_src.bytes[k]};
+    return check_launch(lower, launch_halo_copy(h, lower->stream));
+}

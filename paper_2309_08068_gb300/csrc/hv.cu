@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
         if (m >= a.sv.n_special) return;
         hv_update<S, M, kSpecial>(a, a.sv.cell[m], m);
     } else {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.g.n) return;
+        const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.cell_end) return;
         hv_update<S, M, kSpecial>(a, i, 0);
     }
 }
@@ -280,8 +280,7 @@ __global__ void __launch_bounds__(kBlock) hv_set_kernel(StepArgs a, const float*
 template <int S, int M>
 __global__ void __launch_bounds__(kBlock) hv_reduce_kernel(StepArgs a, double* __restrict__ partials) {
     double w = 0.0, f2 = 0.0;
-    const int n = a.g.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x; i < a.cell_end; i += gridDim.x * blockDim.x) {
         const Neighbourhood h = neighbourhood(a.g, i);
         float4 e[6];
         float2 hy[6];
@@ -487,7 +486,7 @@ int hv_launch_step(const StepArgs& a, cudaStream_t st) {
     with_storage(a.storage, [&](auto sc) {
         with_media(a.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
-            hv_step_kernel<S, M, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+            hv_step_kernel<S, M, false><<<blocks_for(a.cell_end - a.cell_begin), kBlock, 0, st>>>(a);
             launched = 1;
             if (a.sv.n_special > 0) {
                 hv_step_kernel<S, M, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
@@ -598,6 +597,13 @@ int hv_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t s
         hv_adjoint_terminal_kernel<M><<<blocks_for(n_plane), kBlock, 0, st>>>(A, n_plane);
     });
     return 1;
+}
+
+int hv_halo_dirs(int vz_sign, int* dirs) {
+    int k = 0;
+    for (int d = 0; d < 6; ++d)
+        if (kHVAxis[d] == 2 && kHVSign[d] == vz_sign) dirs[k++] = d;
+    return k;
 }
 
 int hv_launch_record_step(const StepArgs& a, cudaStream_t st) {

@@ -93,6 +93,7 @@ struct StepArgs {
     float scale;      // 16-bit storage: stored = f * scale
     float inv_scale;  // 1 / scale
     float* rec;       // adjoint record of this step (recording kernels only): kRecordFloats[model] x n
+    int cell_begin, cell_end;  // cells the step and reduction launches cover (a z-slab skips its ghost planes)
 };
 
 // Per-cell record an adjoint step needs from its forward step: MM E and X = D' - mu0 J_ext / 4, HV E.
@@ -509,6 +510,22 @@ int hv_launch_reduce(const StepArgs& a, double* partials, int n_blocks, double* 
 int launch_reduce_partials(const double* partials, int n_blocks, double* result, cudaStream_t st);
 // Deterministic sum of v[0..count) into result[0] (one block, fixed order; result[1], [2] are 0).
 int launch_sum_doubles(const double* v, int count, double* result, cudaStream_t st);
+
+// Up to 8 independent device-to-device copies in one launch (sizes and addresses multiples of 4 B).
+struct HaloChunk {
+    const char* src;
+    char* dst;
+    long long bytes;
+    int width;  // set by launch_halo_copy
+};
+struct HaloCopy {
+    HaloChunk c[8];
+    int count;
+};
+int launch_halo_copy(HaloCopy h, cudaStream_t st);
+// Directions whose velocity has z component vz_sign (+1 or -1); returns their number.
+int mm_halo_dirs(int vz_sign, int* dirs);
+int hv_halo_dirs(int vz_sign, int* dirs);
 
 // Batched step j: main launch over the first n_tiles tiles, source-cell launch over the first
 // n_stiles special tiles. Returns the number of kernels enqueued.

@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(kBlock, 3) mm_step_kernel(StepArgs a) {
         if (m >= a.sv.n_special) return;
         mm_update<S, M, kSpecial, kRho>(a, a.sv.cell[m], m);
     } else {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.g.n) return;
+        const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= a.cell_end) return;
         mm_update<S, M, kSpecial, kRho>(a, i, 0);
     }
 }
@@ -305,8 +305,7 @@ template <int S, int M, bool kRho>
 __global__ void __launch_bounds__(kBlock) mm_reduce_kernel(StepArgs a, const float* __restrict__ rest1,
                                                            double* __restrict__ partials) {
     double w = 0.0, f2 = 0.0, q = 0.0;
-    const int n = a.g.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x; i < a.cell_end; i += gridDim.x * blockDim.x) {
         const Neighbourhood h = neighbourhood(a.g, i);
         float4 f[12];
         mm_pull<S>(a, h, f);
@@ -548,7 +547,7 @@ int mm_launch_step(const StepArgs& a, cudaStream_t st) {
     with_storage(a.storage, [&](auto sc) {
         with_media(a.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
-            const int nb = blocks_for(a.g.n);
+            const int nb = blocks_for(a.cell_end - a.cell_begin);
             if (rho) mm_step_kernel<S, M, false, true><<<nb, kBlock, 0, st>>>(a);
             else mm_step_kernel<S, M, false, false><<<nb, kBlock, 0, st>>>(a);
             launched = 1;
@@ -683,6 +682,13 @@ int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t s
         mm_adjoint_terminal_kernel<M><<<blocks_for(n_plane), kBlock, 0, st>>>(A, n_plane);
     });
     return 1;
+}
+
+int mm_halo_dirs(int vz_sign, int* dirs) {
+    int k = 0;
+    for (int d = 0; d < 12; ++d)
+        if (kMMV[d][2] == vz_sign) dirs[k++] = d;
+    return k;
 }
 
 int mm_launch_record_step(const StepArgs& a, cudaStream_t st) {

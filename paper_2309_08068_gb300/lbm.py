@@ -39,7 +39,8 @@ class _Media(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("track_rho", ctypes.c_int),
-                ("eps0", ctypes.c_double), ("mu0", ctypes.c_double), ("storage_scale", ctypes.c_double)]
+                ("eps0", ctypes.c_double), ("mu0", ctypes.c_double), ("storage_scale", ctypes.c_double),
+                ("z_ghost", ctypes.c_int)]
 
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
@@ -93,6 +94,10 @@ def load_library(path: str | None = None):
         "lbm_destroy": (I, [P]),
         "lbm_adjoint": (I, [P, I, I, I, I, ctypes.POINTER(D), P, P, I]),
         "lbm_adjoint_release": (I, [P]),
+        "lbm_halo_bytes": (I64, [P]),
+        "lbm_halo_pack": (I, [P, I, P, I]),
+        "lbm_halo_unpack": (I, [P, I, P, I]),
+        "lbm_halo_exchange": (I, [P, P]),
         "lbm_adjoint_workspace_bytes": (I64, [P]),
         "lbm_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
         "lbm_batch_step": (I, [P, ctypes.POINTER(I)]),
@@ -137,7 +142,8 @@ class Lattice:
     """
 
     def __init__(self, model: str, shape, eps_r=None, mu_r=None, sigma=None, *, track_rho: bool = False,
-                 eps0: float = 0.0, mu0: float = 0.0, stream=None, storage: str = "f32", storage_scale: float = 0.0):
+                 eps0: float = 0.0, mu0: float = 0.0, stream=None, storage: str = "f32", storage_scale: float = 0.0,
+                 z_ghost: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Lattice needs a CUDA device; there is no CPU fallback")
@@ -163,8 +169,9 @@ class Lattice:
             raise ValueError("media arrays must all be host or all device arrays")
         media.on_device = on_dev.pop() if on_dev else 0
         opts = _Options(STORAGE[storage], ctypes.c_void_p(self.stream.cuda_stream), int(track_rho), float(eps0),
-                        float(mu0), float(storage_scale))
+                        float(mu0), float(storage_scale), int(z_ghost))
         self.storage = storage
+        self.z_ghost = bool(z_ghost)
         h = ctypes.c_void_p()
         rc = self.lib.lbm_create(MODELS[model], nx, ny, nz, ctypes.byref(media), ctypes.byref(opts), ctypes.byref(h))
         if rc != 0:
@@ -283,6 +290,32 @@ class Lattice:
         self._check(self.lib.lbm_adjoint(self.h, int(steps), int(plane_axis), int(plane_index), int(checkpoint_interval),
                                          ctypes.byref(loss), ge.data_ptr(), gs.data_ptr(), 1))
         return loss.value, ge, gs
+
+    # -- z-slab halo (z_ghost lattices) ---------------------------------------------------------
+    @property
+    def halo_bytes(self) -> int:
+        b = int(self.lib.lbm_halo_bytes(self.h))
+        if b < 0:
+            raise LbmError(b, "halo_bytes: not a z_ghost lattice")
+        return b
+
+    def halo_pack(self, face: int, out=None):
+        """Outgoing populations of face 0 (down) or 1 (up) as a uint8 CUDA tensor (lbm_halo_pack)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.halo_bytes, dtype=torch.uint8, device=self.device)
+        self._check(self.lib.lbm_halo_pack(self.h, int(face), out.data_ptr(), 1))
+        return out
+
+    def halo_unpack(self, face: int, data) -> None:
+        """Write a neighbour's packed face into ghost plane 0 (face 0) or nz - 1 (face 1)."""
+        if data.numel() * data.element_size() != self.halo_bytes or not data.is_cuda:
+            raise ValueError("halo_unpack: need a CUDA buffer of halo_bytes bytes")
+        self._check(self.lib.lbm_halo_unpack(self.h, int(face), data.data_ptr(), 1))
+
+    def halo_exchange(self, upper: "Lattice") -> None:
+        """Exchange across the interface between this slab (below) and `upper` (lbm_halo_exchange)."""
+        self._check(self.lib.lbm_halo_exchange(self.h, upper.h))
 
     def adjoint_release(self) -> None:
         """Free the work space that adjoint() keeps between calls (lbm_adjoint_release)."""

@@ -250,3 +250,20 @@ def random_state(model: str, shape, seed: int, media: str = "random", n_sources:
                                   B0=tuple(rng.standard_normal(3))))
     w = Workload("random_state", model, (nx, ny, nz), 0, eps_r=eps, mu_r=mu, sigma=sig, sources=sources)
     return w, f
+
+
+def slab_case(model: str, shape, seed: int, media: str = "random", amplitude: float = 1.0):
+    """``random_state`` plus sources on two z-columns, so that every plane, and so every slab's
+    boundary planes, holds source cells: a current on the column (1, 2, z) for all z, and imposed
+    fields on (nx - 2, ny - 1, z) for every third z. Returns (Workload, populations)."""
+    nx, ny, nz = shape
+    w, f = random_state(model, shape, seed, media=media, amplitude=amplitude)
+    rng = np.random.default_rng(seed + 1000)
+    z = np.arange(nz, dtype=np.int64)
+    col = (1 % nx) + nx * ((2 % ny) + ny * z)
+    w.sources.append(Source("current", col, TimeFunction("sin", 1.0, 13.0, 0.7), w=rng.standard_normal((nz, 3))))
+    zi = z[::3]
+    imp = ((nx - 2) % nx) + nx * ((ny - 1) + ny * zi)
+    w.sources.append(Source("impose", imp, TimeFunction("sin", 0.8, 17.0, 0.2), E0=tuple(rng.standard_normal(3)),
+                            B0=tuple(rng.standard_normal(3))))
+    return w, f
