@@ -412,38 +412,48 @@ def run_ours(args):
     from paper_2309_08068_gb300.lbm import lattice_from_workload
 
     n_side = args.n
-    ncell = n_side ** 3
+    nz = args.nz or n_side
+    ncell = n_side * n_side * nz
     stream = torch.cuda.Stream()
     lats = {}
     scale = F16_SCALE if args.storage == "f16" else 0.0
     with torch.cuda.stream(stream):
         for model in ("mm", "hv"):
-            w = wl.hertz_dipole(model, n=n_side, period=32.0)
+            w = wl.hertz_dipole(model, n=n_side, period=32.0, nz=nz)
             lats[model] = lattice_from_workload(w, stream=stream, storage=args.storage, storage_scale=scale)
+            lats[model].set_step_fusion(args.fusion)
     torch.cuda.synchronize()
+    fused = {m: L.step_fusion_active for m, L in lats.items()}
 
-    def one_step(ev=None):
+    def chunks(k):
+        """Steps per call: pairs when lbm_step runs two steps per pass, singles otherwise."""
+        if args.fusion == 0:
+            return [1] * k
+        return [2] * (k // 2) + [1] * (k % 2)
+
+    def advance(c, ev=None):
         if ev is not None:
             ev[0].record(stream)
-        lats["mm"].step(1)
+        lats["mm"].step(c)
         if ev is not None:
             ev[1].record(stream)
-        lats["hv"].step(1)
+        lats["hv"].step(c)
         if ev is not None:
             ev[2].record(stream)
 
-    for _ in range(args.warmup):
-        one_step()
+    for c in chunks(args.warmup):
+        advance(c)
     torch.cuda.synchronize()
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    plan = chunks(args.steps)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in plan]
     launches0 = sum(L.launch_count for L in lats.values())
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         start.record(stream)
-        for k in range(args.steps):
-            one_step(events[k])
+        for c, ev in zip(plan, events):
+            advance(c, ev)
         stop.record(stream)
         torch.cuda.synchronize()
     barrier(world)
@@ -451,6 +461,22 @@ def run_ours(args):
     elapsed_ms = start.elapsed_time(stop)
     mm_ms = sum(e[0].elapsed_time(e[1]) for e in events) / args.steps
     hv_ms = sum(e[1].elapsed_time(e[2]) for e in events) / args.steps
+    for L in lats.values():
+        L.sync()  # also reports a pass whose dependency wait timed out
+
+    # the same lattices one step per launch (the single-step kernels), for reference
+    single = {}
+    for model, L in lats.items():
+        L.set_step_fusion(0)
+        k1 = max(10, min(args.steps, 50))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.step(k1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        single[model] = e0.elapsed_time(e1) / k1
+        L.set_step_fusion(args.fusion)
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     finite = all(L.check_finite() for L in lats.values())
 
@@ -460,23 +486,25 @@ def run_ours(args):
         variants[st] = {}
         for model in ("mm", "hv"):
             with torch.cuda.stream(stream):
-                w = wl.hertz_dipole(model, n=n_side, period=32.0)
+                w = wl.hertz_dipole(model, n=n_side, period=32.0, nz=nz)
                 Lv = lattice_from_workload(w, stream=stream, storage=st,
                                            storage_scale=F16_SCALE if st == "f16" else 0.0)
-            for _ in range(args.warmup):
-                Lv.step(1)
+            Lv.set_step_fusion(args.fusion)
+            for c in chunks(args.warmup):
+                Lv.step(c)
             kv = max(10, min(args.steps, 200))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            for _ in range(kv):
-                Lv.step(1)
+            for c in chunks(kv):
+                Lv.step(c)
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / kv
-            nbytes = BYTES_PER_CELL[model] // 2
+            fv = Lv.step_fusion_active
+            nbytes = BYTES_PER_CELL[model] // 2 // (2 if fv else 1)  # per cell and step
             variants[st][model] = {"MLUPS": round(ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
-                                   "bytes_per_cell": nbytes,
+                                   "two_steps_per_pass": fv, "bytes_per_cell_step": nbytes,
                                    "algorithmic_GBps": round(nbytes * ncell / (ms * 1e-3) / 1e9, 1),
                                    "steps_timed": kv}
             Lv.close()
@@ -495,9 +523,9 @@ def run_ours(args):
     t0 = time.perf_counter()
     for m, L in lats.items():
         L.lib.lbm_init_fields(L.h, pinned_E.data_ptr(), pinned_B.data_ptr(), 0)
-    for _ in range(e2e_steps):
-        lats["mm"].step(1)
-        lats["hv"].step(1)
+    for c in chunks(e2e_steps):
+        lats["mm"].step(c)
+        lats["hv"].step(c)
     for m, L in lats.items():
         L._check(L.lib.lbm_fields(L.h, 3, out[m].ctypes.data, 0))
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
@@ -513,11 +541,17 @@ def run_ours(args):
     value = job_value(2 * ncell, args.steps, world, elapsed_ms * 1e-3)
     peak, peak_kind = hbm_peak()
     shrink = 4 // POPULATION_BYTES[args.storage]
-    bpc = {m: BYTES_PER_CELL[m] // shrink for m in BYTES_PER_CELL}
+    # Algorithmic HBM bytes per cell and step: one read and one write of the populations per step,
+    # or per pair of steps when a pass runs two (the intermediate step stays on chip).
+    bpc1 = {m: BYTES_PER_CELL[m] // shrink for m in BYTES_PER_CELL}
+    bpc = {m: bpc1[m] // (2 if fused[m] else 1) for m in bpc1}
     mm_gbs = bpc["mm"] * ncell / (mm_ms * 1e-3) / 1e9
     hv_gbs = bpc["hv"] * ncell / (hv_ms * 1e-3) / 1e9
-    traffic = ncu_traffic("mm_step_kernel", ncell) if args.storage == "f32" else None
-    hv_traffic = ncu_traffic("hv_step_kernel", ncell) if args.storage == "f32" else None
+    kname = {m: (f"{m}_fused2_kernel" if fused[m] else f"{m}_step_kernel") for m in fused}
+    # ncu traffic is per launch: a fused launch covers two steps
+    traffic = ncu_traffic(kname["mm"], ncell) if args.storage == "f32" else None
+    hv_traffic = ncu_traffic(kname["hv"], ncell) if args.storage == "f32" else None
+    single_gbs = {m: bpc1[m] * ncell / (single[m] * 1e-3) / 1e9 for m in single}
     cores = cpu_cores()
     cpu_mlups, cpu_steps, cpu_s = oracle_mlups(64, args.cpu_seconds, cores)
     line = {
@@ -526,19 +560,30 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "storage": args.storage,
         "data": "synthetic",
-        "config": {"workload": f"hertz_dipole_{n_side}^3_mm+hv", "cells_per_model": ncell,
+        "config": {"workload": (f"hertz_dipole_{n_side}^3_mm+hv" if nz == n_side
+                                else f"hertz_dipole_{n_side}x{n_side}x{nz}_mm+hv"), "cells_per_model": ncell,
                    "step": "one MM step + one HV step, each on its own lattice", "period": 32, "J0": 1e-4,
+                   "calls": ("lbm_step(ctx, 2): two steps per pass where it applies" if args.fusion
+                             else "lbm_step(ctx, 1)"),
                    "l2": "inputs larger than L2 (MM 3.2 GB, HV 2.4 GB per population buffer)",
                    "parallelism": f"independent lattices per rank x{world}"},
         "per_model": {
             "mm": {"MLUPS": round(ncell / (mm_ms * 1e-3) / 1e6, 2), "ms_per_step": round(mm_ms, 4),
-                   "algorithmic_GBps": round(mm_gbs, 1), "bytes_per_cell": bpc["mm"]},
+                   "two_steps_per_pass": fused["mm"], "kernel": kname["mm"],
+                   "algorithmic_GBps": round(mm_gbs, 1), "bytes_per_cell_step": bpc["mm"]},
             "hv": {"MLUPS": round(ncell / (hv_ms * 1e-3) / 1e6, 2), "ms_per_step": round(hv_ms, 4),
-                   "algorithmic_GBps": round(hv_gbs, 1), "bytes_per_cell": bpc["hv"],
+                   "two_steps_per_pass": fused["hv"], "kernel": kname["hv"],
+                   "algorithmic_GBps": round(hv_gbs, 1), "bytes_per_cell_step": bpc["hv"],
                    "frac": round(hv_gbs / peak, 4),
                    "traffic": None if hv_traffic is None else round(hv_traffic)},
         },
-        "roofline": {"bound": "hbm", "kernel": "mm_step_kernel (+ source-cell launch)",
+        "single_step_kernels": {
+            m: {"ms_per_step": round(single[m], 4), "MLUPS": round(ncell / (single[m] * 1e-3) / 1e6, 2),
+                "bytes_per_cell_step": bpc1[m], "algorithmic_GBps": round(single_gbs[m], 1),
+                "frac": round(single_gbs[m] / peak, 4)} for m in single},
+        "roofline": {"bound": "hbm",
+                     "kernel": kname["mm"] + (" (two steps per launch, sources included)" if fused["mm"]
+                                              else " (+ source-cell launch)"),
                      "achieved": round(mm_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(mm_gbs / peak, 4),
                      "traffic": None if traffic is None else round(traffic)},
@@ -571,7 +616,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--nz", type=int, default=0, help="z extent of the timed lattices (default n: a cube)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--fusion", type=int, choices=[0, 1, 2], default=1,
+                    help="lbm_set_step_fusion mode of the timed lattices: 0 one launch per step, 1 two steps per "
+                         "pass where the intermediate planes fit in L2 (default), 2 whenever possible")
     ap.add_argument("--slab-steps", type=int, default=50,
                     help="steps of the z-slab decomposition measurement on the dipole lattice (0 skips it)")
     ap.add_argument("--adjoint-steps", type=int, default=1000,

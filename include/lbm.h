@@ -207,6 +207,26 @@ int lbm_sync(lbm_ctx* ctx);
 /* Free the context and its device memory. NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);
 
+/* Two time steps per pass. A step reads only a cell's 3 x 3 x 3 neighbourhood (advection, Sections
+ * II and III), so lbm_step(ctx, n >= 2) can run steps t and t + 1 as one wavefront along z: one
+ * persistent launch updates plane p at step t into a small ring of intermediate planes, and plane
+ * p at step t + 1 once planes p - 1, p, p + 1 of step t exist. The ring is meant to stay in L2, so
+ * each pair of steps reads and writes the populations in HBM once instead of twice. The results
+ * equal single steps bit for bit (same arithmetic; the intermediate planes hold the populations in
+ * the context's storage format).
+ *   mode 0: never; 1 (default): when the intermediate planes (R + 2 planes of populations: R = 5
+ *   for MM, 6 for HV) fit in three quarters of L2 and a plane has at least 256 cells per SM;
+ *   2: whenever a plane has that many cells.
+ * Never for z_ghost slabs or track_rho contexts, nor with nz < 4 (MM) or 5 (HV). The pass's dependency waits are
+ * bounded (2 s); if one expires the pass stops, and the next lbm_sync, lbm_reduce or host-side
+ * lbm_fields / lbm_get_populations returns LBM_ECUDA. Odd n ends with one single step. The pass
+ * allocates its intermediate planes and counters on first use (kept until lbm_destroy).
+ * tile_cells: cells per work item of a pass, a multiple of 256 up to 4096; 0 keeps the current
+ * value (default 256 for MM, 512 for HV, the fastest on GB300). */
+int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells);
+/* 1 when lbm_step would run pairs of steps as single passes, 0 when not (negative on error). */
+int lbm_step_fusion_active(lbm_ctx* ctx);
+
 /* Loss and gradient over the next `steps` time steps (inverse material design; the paper itself
  * only runs forward). From the current populations, the context advances `steps` steps exactly as
  * lbm_step does, and

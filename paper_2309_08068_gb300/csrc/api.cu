@@ -77,6 +77,18 @@ struct lbm_ctx {
     // staging of a packed halo face for host-side lbm_halo_pack / lbm_halo_unpack
     void* halo_stage = nullptr;
     size_t halo_stage_bytes = 0;
+    // two steps per pass (lbm_step with n >= 2): mode, intermediate planes, counters
+    int fusion = 1;                // 0 off, 1 when the ring fits the L2 budget, 2 whenever possible
+    int fused_tile = 0;            // cells per work item of a pass (0: the model's default)
+    void* fused_planes = nullptr;  // R ring slots + the slots of planes 0 and nz - 1
+    size_t fused_planes_bytes = 0;
+    int* fused_ctrl = nullptr;     // item counter, 2 nz tile counters, abort, 2 nz + 2 nz tiles flags
+    int fused_epoch = 0;           // number of the last pass launched
+    int* d_plane_special = nullptr;
+    int plane_special_version = -1;
+    int sources_version = 0;
+    int fused_pending = 0;         // a pass ran since the abort flag was last read
+    std::vector<int> h_cell;       // host copy of the special-cell list (sorted)
     int64_t t = 0;
     int64_t launches = 0;
     std::string err;
@@ -192,7 +204,160 @@ void free_dev(T*& p) {
     p = nullptr;
 }
 
+// --- two steps per pass ------------------------------------------------------------------------
+// Pass shape per model, measured on GB300 (256^3 dipole): the ring slots R (planes 1 .. nz - 2),
+// the lookahead L of A phases over B phases (R >= L + 1), and the cells per work item. Deeper
+// rings let more work run at once until the ring no longer stays in L2.
+struct FusedShape {
+    int R, L, tile;
+};
+constexpr FusedShape kFusedMM{5, 3, 256};
+constexpr FusedShape kFusedHV{6, 4, 512};
+static_assert(kFusedMM.L >= 2 && kFusedMM.R >= kFusedMM.L + 1 && kFusedHV.L >= 2 && kFusedHV.R >= kFusedHV.L + 1,
+              "the pass order needs R >= L + 1 >= 3");
+constexpr long long kFusedTimeoutNs = 2000000000;  // a dependency wait longer than this aborts
+
+FusedShape fused_shape(const lbm_ctx* c) { return c->model == LBM_MM ? kFusedMM : kFusedHV; }
+
+int fused_tile_cells(const lbm_ctx* c) { return c->fused_tile ? c->fused_tile : fused_shape(c).tile; }
+int fused_tiles(const lbm_ctx* c) { return (c->g.nx * c->g.ny + fused_tile_cells(c) - 1) / fused_tile_cells(c); }
+
+// Pass control block: [item counter][2 nz tile counters][abort][2 nz source-item flags]
+// [2 nz x tiles tile flags]. The first 1 + 2 nz are zeroed before every pass.
+size_t fused_ctrl_ints(const lbm_ctx* c) {
+    const size_t nz = (size_t)c->g.nz, tiles = (size_t)fused_tiles(c);
+    return 1 + 2 * nz + 1 + 2 * nz + 2 * nz * tiles;
+}
+
+size_t fused_plane_bytes(const lbm_ctx* c) {
+    const size_t nxy = (size_t)c->g.nx * c->g.ny;
+    return (group_bytes(c->model, c->storage) + (c->model == LBM_HV ? pair_bytes(c->storage) : 0)) * nxy;
+}
+
+// Pairs of steps run as one pass when the wavefront has enough tiles per plane to fill the GPU and
+// (mode 1) the intermediate planes fit in three quarters of L2, where they are meant to stay.
+bool fusion_eligible(const lbm_ctx* c) {
+    if (c->fusion == 0 || c->z_ghost || c->track_rho || c->g.nz < std::max(3, fused_shape(c).L + 1)) return false;
+    int dev = 0, sms = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (c->g.nx * c->g.ny < sms * kBlock) return false;
+    if (c->fusion == 1 && (fused_shape(c).R + 2) * fused_plane_bytes(c) > (size_t)l2 / 4 * 3) return false;
+    return true;
+}
+
+int ensure_fused(lbm_ctx* c) {
+    const size_t need = (fused_shape(c).R + 2) * fused_plane_bytes(c);
+    if (c->fused_planes_bytes < need) {
+        free_dev(c->fused_planes);
+        c->fused_planes_bytes = 0;
+        if (cudaMalloc(&c->fused_planes, need) != cudaSuccess) {
+            cudaGetLastError();
+            c->fused_planes = nullptr;
+            return fail(c, LBM_ENOMEM, "lbm_step: cannot allocate %zu bytes of intermediate planes", need);
+        }
+        c->fused_planes_bytes = need;
+    }
+    if (!c->fused_ctrl) {
+        const size_t ints = fused_ctrl_ints(c);
+        if (cudaMalloc(&c->fused_ctrl, sizeof(int) * ints) != cudaSuccess) {
+            cudaGetLastError();
+            c->fused_ctrl = nullptr;
+            return fail(c, LBM_ENOMEM, "lbm_step: cannot allocate the pass counters");
+        }
+        CUDA_TRY(c, cudaMemsetAsync(c->fused_ctrl, 0, sizeof(int) * ints, c->stream));
+        c->fused_epoch = 0;
+    }
+    if (c->plane_special_version != c->sources_version || !c->d_plane_special) {
+        // offsets of each plane's cells in the sorted special-cell list
+        const int nz = c->g.nz, nxy = c->g.nx * c->g.ny;
+        std::vector<int> off((size_t)nz + 1, 0);
+        size_t m = 0;
+        for (int p = 0; p <= nz; ++p) {
+            while (m < c->h_cell.size() && c->h_cell[m] < p * nxy) ++m;
+            off[(size_t)p] = (int)m;
+        }
+        if (!c->d_plane_special && cudaMalloc(&c->d_plane_special, sizeof(int) * ((size_t)nz + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            c->d_plane_special = nullptr;
+            return fail(c, LBM_ENOMEM, "lbm_step: cannot allocate the plane offsets");
+        }
+        CUDA_TRY(c, cudaMemcpy(c->d_plane_special, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+        c->plane_special_version = c->sources_version;
+    }
+    return LBM_OK;
+}
+
+int fused_pass(lbm_ctx* c) {
+    const int in = c->cur, out = 1 - c->cur;
+    const int nz = c->g.nz;
+    StepArgs aA = base_args(c), aB = base_args(c);
+    bind_buffers(c, aA, in, out);
+    bind_buffers(c, aB, in, out);
+    fill_scalars(c, aA, c->t + 1);
+    fill_scalars(c, aB, c->t + 2);
+    const size_t nxy = (size_t)c->g.nx * c->g.ny;
+    const size_t g_plane = group_bytes(c->model, c->storage) * nxy;
+    const size_t p_plane = c->model == LBM_HV ? pair_bytes(c->storage) * nxy : 0;
+    const FusedShape shape = fused_shape(c);
+    const int R = shape.R;
+    char* base = static_cast<char*>(c->fused_planes);
+    char* groups = base;                        // R + 2 group planes
+    char* pairs = base + (R + 2) * g_plane;     // R + 2 pair planes (HV)
+    FusedArgs F;
+    memset(&F, 0, sizeof(F));
+    F.ring = groups;
+    F.lo = groups + R * g_plane;
+    F.hi = groups + (R + 1) * g_plane;
+    if (p_plane) {
+        F.ring2 = pairs;
+        F.lo2 = pairs + R * p_plane;
+        F.hi2 = pairs + (R + 1) * p_plane;
+    }
+    F.R = R;
+    F.L = shape.L;
+    F.tile_cells = fused_tile_cells(c);
+    F.tiles = fused_tiles(c);
+    F.epoch = ++c->fused_epoch;
+    F.next = c->fused_ctrl;
+    F.count = c->fused_ctrl + 1;
+    F.abort = c->fused_ctrl + 1 + 2 * nz;
+    F.fix_flag = c->fused_ctrl + 2 + 2 * nz;
+    F.tile_flag = c->fused_ctrl + 2 + 4 * nz;
+    F.plane_special = c->d_plane_special;
+    F.timeout_ns = kFusedTimeoutNs;
+    CUDA_TRY(c, cudaMemsetAsync(c->fused_ctrl, 0, sizeof(int) * (1 + 2 * (size_t)nz), c->stream));
+    const int launched = c->model == LBM_MM ? mm_launch_fused2(aA, aB, F, c->stream) : hv_launch_fused2(aA, aB, F, c->stream);
+    int rc = check_launch(c, launched);
+    if (rc != LBM_OK) return rc;
+    c->fused_pending = 1;
+    c->cur = out;
+    c->t += 2;
+    return LBM_OK;
+}
+
+// Reports (once) a two-step pass whose dependency wait timed out since the last check.
+int check_fused_abort(lbm_ctx* c) {
+    if (!c->fused_pending || !c->fused_ctrl) return LBM_OK;
+    int flag = 0;
+    int* abort = c->fused_ctrl + 1 + 2 * c->g.nz;
+    CUDA_TRY(c, cudaMemcpyAsync(&flag, abort, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->fused_pending = 0;
+    if (flag) {
+        CUDA_TRY(c, cudaMemsetAsync(abort, 0, sizeof(int), c->stream));
+        return fail(c, LBM_ECUDA, "a two-step pass stopped: a dependency wait exceeded its time limit");
+    }
+    return LBM_OK;
+}
+
 void free_sources_device(lbm_ctx* c) {
+    c->sources_version += 1;
+    c->h_cell.clear();
     free_dev(c->d_cell);
     free_dev(c->d_entry_begin);
     free_dev(c->d_entry_src);
@@ -260,6 +425,7 @@ int rebuild_sources(lbm_ctx* c) {
     }
     CUDA_TRY(c, cudaMemcpy(c->d_impose_mask, mask.data(), sizeof(uint32_t) * ns, cudaMemcpyHostToDevice));
     c->n_special = ns;
+    c->h_cell = cell;
     return LBM_OK;
 }
 
@@ -383,6 +549,10 @@ void release(lbm_ctx* c) {
     c->adj_ws_bytes = 0;
     free_dev(c->halo_stage);
     c->halo_stage_bytes = 0;
+    free_dev(c->fused_planes);
+    c->fused_planes_bytes = 0;
+    free_dev(c->fused_ctrl);
+    free_dev(c->d_plane_special);
 }
 
 // Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
@@ -609,8 +779,14 @@ int lbm_step(lbm_ctx* ctx, int n) {
     if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n must be >= 0");
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    int s = 0;
+    if (n >= 2 && fusion_eligible(ctx)) {
+        if ((rc = ensure_fused(ctx)) != LBM_OK) return rc;
+        for (; s + 2 <= n; s += 2)
+            if ((rc = fused_pass(ctx)) != LBM_OK) return rc;
+    }
     StepArgs a = base_args(ctx);
-    for (int s = 0; s < n; ++s) {
+    for (; s < n; ++s) {
         const int in = ctx->cur, out = 1 - ctx->cur;
         bind_buffers(ctx, a, in, out);
         fill_scalars(ctx, a, ctx->t + 1);
@@ -628,6 +804,7 @@ int lbm_fields(lbm_ctx* ctx, unsigned mask, float* out, int on_device) {
     if (mask == 0 || (mask & ~31u)) return fail(ctx, LBM_EINVAL, "lbm_fields: bad mask 0x%x", mask);
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    if (!on_device && (rc = check_fused_abort(ctx)) != LBM_OK) return rc;
     int nf = 0;
     for (int b = 0; b < 5; ++b) nf += (mask >> b) & 1;
     const size_t cnt = 3 * (size_t)ctx->g.n * nf;
@@ -666,6 +843,7 @@ int lbm_get_populations(lbm_ctx* ctx, float* out, int on_device) {
     if (!out) return fail(ctx, LBM_EINVAL, "lbm_get_populations: out is NULL");
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    if (!on_device && (rc = check_fused_abort(ctx)) != LBM_OK) return rc;
     const size_t cnt = (size_t)lbm_num_populations(ctx->model) * ctx->g.n;
     float* dev = out;
     if (!on_device && cudaMalloc(&dev, sizeof(float) * cnt) != cudaSuccess) {
@@ -714,6 +892,7 @@ int lbm_reduce(lbm_ctx* ctx, double out[3]) {
     if (!out) return fail(ctx, LBM_EINVAL, "lbm_reduce: out is NULL");
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    if ((rc = check_fused_abort(ctx)) != LBM_OK) return rc;
     const int ns_blocks = ctx->n_special > 0 ? (ctx->n_special + kBlock - 1) / kBlock : 0;
     if ((rc = ensure_partials(ctx, ctx->reduce_blocks + ns_blocks)) != LBM_OK) return rc;
     StepArgs a = base_args(ctx);
@@ -746,7 +925,30 @@ int lbm_sync(lbm_ctx* ctx) {
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_fused_abort(ctx);
+}
+
+int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells) {
+    if (!ctx) return LBM_EINVAL;
+    if (mode < 0 || mode > 2) return fail(ctx, LBM_EINVAL, "lbm_set_step_fusion: mode must be 0, 1 or 2");
+    if (tile_cells < 0 || tile_cells % kBlock != 0 || tile_cells > 16 * kBlock)
+        return fail(ctx, LBM_EINVAL, "lbm_set_step_fusion: tile_cells must be 0 or a multiple of %d up to %d", kBlock,
+                    16 * kBlock);
+    if (tile_cells != 0 && tile_cells != fused_tile_cells(ctx)) {
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        else cudaDeviceSynchronize();
+        free_dev(ctx->fused_ctrl);  // its flag array depends on the tile count
+        ctx->fused_tile = tile_cells;
+    }
+    ctx->fusion = mode;
     return LBM_OK;
+}
+
+int lbm_step_fusion_active(lbm_ctx* ctx) {
+    if (!ctx) return LBM_EINVAL;
+    int rc;
+    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
+    return fusion_eligible(ctx) ? 1 : 0;
 }
 
 }  // extern "C"

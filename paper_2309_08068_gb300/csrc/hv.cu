@@ -116,13 +116,25 @@ __device__ __forceinline__ float3 hv_h(float3 B, const MatCoef& mat) {
     return make_float3(div_rn(B.x, mu, inv_mu), div_rn(B.y, mu, inv_mu), div_rn(B.z, mu, inv_mu));
 }
 
+// Where a step reads its populations and writes its results: the context's A/B buffers.
+struct HVBuffers {
+    template <int S>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) const {
+        hv_pull<S>(a, h, e, hy);
+    }
+    template <int S>
+    __device__ void put(const StepArgs& a, int k, int i, float4 e, float2 hy) const {
+        hv_put<S>(a, k, i, e, hy);
+    }
+};
+
 // Update of cell i; m is its index in the special-cell list when kSpecial.
-template <int S, int M, bool kSpecial, bool kRecord = false>
-__device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m) {
+template <int S, int M, bool kSpecial, bool kRecord = false, class IO = HVBuffers>
+__device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m, const IO& io = IO{}) {
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 e[6];
     float2 hy[6];
-    hv_pull<S>(a, h, e, hy);
+    io.template pull<S>(a, h, e, hy);
     const MatCoef mat = load_coef<kModelHV, M>(a.media, i, a.eps0, a.mu0);
     CellSource cs;
     float3 jext = make_float3(0.f, 0.f, 0.f);
@@ -155,7 +167,7 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m) {
                 ho = make_float3(b6.x + 0.5f * cE.x, b6.y + 0.5f * cE.y, b6.z + 0.5f * cE.z);
             }
         }
-        hv_put<S>(a, k, i, make_float4(eo.x, eo.y, eo.z, ho.x), make_float2(ho.y, ho.z));
+        io.template put<S>(a, k, i, make_float4(eo.x, eo.y, eo.z, ho.x), make_float2(ho.y, ho.z));
     });
     if constexpr (kRecord) {  // what the adjoint of this step needs: E
         const int n = a.g.n;
@@ -163,6 +175,103 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m) {
         a.rec[n + i] = F.E.y;
         a.rec[2 * n + i] = F.E.z;
     }
+}
+
+// Two steps per pass (see FusedArgs): phase A streams the A/B buffers in once and writes the
+// intermediate plane, phase B pulls from the intermediate planes (L2 loads) and streams the other
+// A/B buffers out. The arithmetic is hv_update's, so the results equal two single steps bit for bit.
+template <int S>
+struct HVToRing {
+    using T4 = typename Pack4<S>::T;
+    using T2 = typename Pack2<S>::T;
+    T4* plane;
+    T2* plane2;
+    int base, nxy;
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) const {
+        const T4* __restrict__ ein = static_cast<const T4*>(a.fin);
+        const T2* __restrict__ hin = static_cast<const T2*>(a.fin2);
+        static_for<0, 6>([&](auto ic) {
+            constexpr int k = decltype(ic)::value;
+            const int src = pull_index<k>(h);
+            e[k] = Pack4<S>::unpack(__ldcs(ein + (size_t)k * a.g.n + src), a.inv_scale);
+            hy[k] = Pack2<S>::unpack(__ldcs(hin + (size_t)k * a.g.n + src), a.inv_scale);
+        });
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int k, int i, float4 e, float2 hy) const {
+        __stcg(plane + (size_t)k * nxy + (i - base), Pack4<S>::pack(e, a.scale));
+        __stcg(plane2 + (size_t)k * nxy + (i - base), Pack2<S>::pack(hy, a.scale));
+    }
+};
+
+template <int S>
+struct HVFromRing {
+    using T4 = typename Pack4<S>::T;
+    using T2 = typename Pack2<S>::T;
+    const T4* plane[3];  // slots of planes z - 1, z, z + 1
+    const T2* plane2[3];
+    int nxy;
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) const {
+        static_for<0, 6>([&](auto ic) {
+            constexpr int k = decltype(ic)::value;
+            constexpr int ax = kHVAxis[k], sg = kHVSign[k];
+            constexpr int sx = ax == 0 ? -sg : 0, sy = ax == 1 ? -sg : 0, sz = ax == 2 ? -sg : 0;
+            const int off = (int)((size_t)k * nxy) + h.xo[sx + 1] + h.yo[sy + 1];
+            e[k] = Pack4<S>::unpack(__ldcg(plane[sz + 1] + off), a.inv_scale);
+            hy[k] = Pack2<S>::unpack(__ldcg(plane2[sz + 1] + off), a.inv_scale);
+        });
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int k, int i, float4 e, float2 hy) const {
+        T4* __restrict__ eout = static_cast<T4*>(a.fout);
+        T2* __restrict__ hout = static_cast<T2*>(a.fout2);
+        __stcs(eout + (size_t)k * a.g.n + i, Pack4<S>::pack(e, a.scale));
+        __stcs(hout + (size_t)k * a.g.n + i, Pack2<S>::pack(hy, a.scale));
+    }
+};
+
+template <int S, int M>
+__global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA, StepArgs aB, FusedArgs F) {
+    using T4 = typename Pack4<S>::T;
+    using T2 = typename Pack2<S>::T;
+    const int nz = aA.g.nz, nxy = aA.g.nx * aA.g.ny;
+    auto slot = [&](int p) -> T4* {
+        if (p == 0) return static_cast<T4*>(F.lo);
+        if (p == nz - 1) return static_cast<T4*>(F.hi);
+        return static_cast<T4*>(F.ring) + (size_t)(p % F.R) * 6 * nxy;
+    };
+    auto slot2 = [&](int p) -> T2* {
+        if (p == 0) return static_cast<T2*>(F.lo2);
+        if (p == nz - 1) return static_cast<T2*>(F.hi2);
+        return static_cast<T2*>(F.ring2) + (size_t)(p % F.R) * 6 * nxy;
+    };
+    fused_loop(F, aA.g.nx, nxy, nz, [&](int type, int p, int j) {
+        const int base = p * nxy;
+        if (type == kPhaseA) {
+            const HVToRing<S> io{slot(p), slot2(p), base, nxy};
+            if (j < F.tiles) {
+                const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
+                for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
+                    hv_update<S, M, false, false>(aA, i, 0, io);
+            } else {
+                for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
+                    hv_update<S, M, true, false>(aA, aA.sv.cell[m], m, io);
+            }
+        } else {
+            const int pm = (p + nz - 1) % nz, pp = (p + 1) % nz;
+            const HVFromRing<S> io{{slot(pm), slot(p), slot(pp)}, {slot2(pm), slot2(p), slot2(pp)}, nxy};
+            if (j < F.tiles) {
+                const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
+                for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
+                    hv_update<S, M, false, false>(aB, i, 0, io);
+            } else {
+                for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
+                    hv_update<S, M, true, false>(aB, aB.sv.cell[m], m, io);
+            }
+        }
+    });
 }
 
 template <int S, int M, bool kSpecial>
@@ -595,6 +704,28 @@ int hv_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t s
     with_media(A.a.media_mode, [&](auto mc) {
         constexpr int M = decltype(mc)::value;
         hv_adjoint_terminal_kernel<M><<<blocks_for(n_plane), kBlock, 0, st>>>(A, n_plane);
+    });
+    return 1;
+}
+
+int hv_fused2_occupancy(int storage, int media_mode) {
+    int blocks = 0;
+    with_storage(storage, [&](auto sc) {
+        with_media(media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, hv_fused2_kernel<S, M>, kFusedThreads, 0);
+        });
+    });
+    return blocks;
+}
+
+int hv_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, cudaStream_t st) {
+    const int grid = fused_grid(hv_fused2_occupancy(aA.storage, aA.media_mode));
+    with_storage(aA.storage, [&](auto sc) {
+        with_media(aA.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            hv_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
+        });
     });
     return 1;
 }

@@ -120,12 +120,14 @@ struct Pack2;
 template <>
 struct Pack4<kF32> {
     using T = float4;
+    __device__ static float4 unpack(T u, float) { return u; }
     __device__ static float4 load(const T* p, float) { return __ldg(p); }
     __device__ static T pack(float4 v, float) { return v; }
 };
 template <>
 struct Pack2<kF32> {
     using T = float2;
+    __device__ static float2 unpack(T u, float) { return u; }
     __device__ static float2 load(const T* p, float) { return __ldg(p); }
     __device__ static T pack(float2 v, float) { return v; }
 };
@@ -133,8 +135,8 @@ struct Pack2<kF32> {
 template <>
 struct Pack4<kF16> {
     using T = uint2;
-    __device__ static float4 load(const T* p, float inv) {
-        const uint2 u = __ldg(p);
+    __device__ static float4 load(const T* p, float inv) { return unpack(__ldg(p), inv); }
+    __device__ static float4 unpack(T u, float inv) {
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
         return make_float4(a.x * inv, a.y * inv, b.x * inv, b.y * inv);
@@ -148,8 +150,8 @@ struct Pack4<kF16> {
 template <>
 struct Pack2<kF16> {
     using T = uint32_t;
-    __device__ static float2 load(const T* p, float inv) {
-        const uint32_t u = __ldg(p);
+    __device__ static float2 load(const T* p, float inv) { return unpack(__ldg(p), inv); }
+    __device__ static float2 unpack(T u, float inv) {
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u));
         return make_float2(a.x * inv, a.y * inv);
     }
@@ -162,8 +164,8 @@ struct Pack2<kF16> {
 template <>
 struct Pack4<kBF16> {
     using T = uint2;
-    __device__ static float4 load(const T* p, float inv) {
-        const uint2 u = __ldg(p);
+    __device__ static float4 load(const T* p, float inv) { return unpack(__ldg(p), inv); }
+    __device__ static float4 unpack(T u, float inv) {
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
         const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
         return make_float4(a.x * inv, a.y * inv, b.x * inv, b.y * inv);
@@ -177,8 +179,8 @@ struct Pack4<kBF16> {
 template <>
 struct Pack2<kBF16> {
     using T = uint32_t;
-    __device__ static float2 load(const T* p, float inv) {
-        const uint32_t u = __ldg(p);
+    __device__ static float2 load(const T* p, float inv) { return unpack(__ldg(p), inv); }
+    __device__ static float2 unpack(T u, float inv) {
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
         return make_float2(a.x * inv, a.y * inv);
     }
@@ -203,6 +205,14 @@ inline void with_media(int m, F&& f) {
 }
 
 inline int blocks_for(int n) { return (n + kBlock - 1) / kBlock; }
+
+// Grid of a persistent launch: resident blocks per SM x the current device's SM count.
+inline int fused_grid(int blocks_per_sm) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, blocks_per_sm) * std::max(1, sms);
+}
 
 // --- compile-time loop ---------------------------------------------------------------------
 template <int I, int N, class F>
@@ -490,6 +500,271 @@ __device__ __forceinline__ void add_plane_loss(const AdjointArgs& A, const Neigh
     else *slot += e2;
 }
 
+// --- two time steps per pass over the populations ---------------------------------------------
+// A step of cell x reads only the populations of its 3 x 3 x 3 neighbourhood. So step t + 1 of a
+// cell can run as soon as step t has produced its 27 neighbours. One persistent launch runs both
+// steps as a wavefront along z:
+//   phase A(p): step t of plane p, from the A/B buffer into an intermediate plane;
+//   phase B(p): step t + 1 of plane p, from the intermediate planes p - 1, p, p + 1 into the other
+//     A/B buffer.
+// The intermediate planes of 1 .. nz - 2 live in a ring of R plane slots, small enough to stay in
+// L2. Planes 0 and nz - 1 are needed at both ends of the periodic wavefront, so they have slots
+// of their own. Each step's HBM traffic is then one read or one write of the populations instead
+// of both.
+// Phases run in the order A(nz-1), A(0), .., A(L-1), then B(k), A(k + L) for k = 0 .. nz-2-L,
+// then the remaining B phases (L >= 2: B(k) needs A(k + 1); R >= L + 1 keeps every wait on an
+// earlier item). A phase is `tiles` tiles of tile_cells consecutive cells of its plane, then one item for
+// the plane's source cells. Blocks take items in that order from a counter, and an item waits
+// only for items taken before it:
+//   * tile j of B(p) waits for the tiles of A(p - 1), A(p), A(p + 1) holding the rows next to its
+//     own (the cells it pulls from), and for those planes' source-cell items;
+//   * tile j of A(p) waits for the same neighbourhood of tiles of the three B phases that read the
+//     slot's previous plane, p - R;
+//   * a source-cell item waits for every tile of its own phase.
+// Tiles publish the pass number in a flag of their own, so the flags need no reset between passes.
+// Every wait has a time limit; past it the pass sets `abort` and every block stops.
+struct FusedArgs {
+    void* ring;   // R slots of one plane of intermediate populations (the model's group layout)
+    void* lo;     // slot of plane 0
+    void* hi;     // slot of plane nz - 1
+    void* ring2;  // HV: the same for the pair arrays (null for MM)
+    void* lo2;
+    void* hi2;
+    int R;
+    int L;                      // A runs L planes ahead of B in the item order (R >= L + 1)
+    int tile_cells;             // cells per tile: a multiple of kBlock (each thread takes every kBlock-th)
+    int tiles;                  // tiles per plane
+    int epoch;                  // this pass's number (>= 1); flags hold the last pass they finished
+    int* next;                  // item counter (zero at launch)
+    int* count;                 // 2 nz finished-tile counters, A then B (zero at launch)
+    int* tile_flag;             // 2 nz tiles flags, A then B
+    int* fix_flag;              // 2 nz source-cell item flags, A then B
+    int* abort;                 // set when a wait timed out
+    const int* plane_special;   // nz + 1 offsets of each plane's cells in the special-cell list
+    long long timeout_ns;
+};
+
+enum { kPhaseA = 0, kPhaseB = 1 };
+
+__device__ __forceinline__ void fused_phase(int q, int nz, int L, int* type, int* plane) {
+    if (q < L + 1) {
+        *type = kPhaseA;
+        *plane = q == 0 ? nz - 1 : q - 1;
+        return;
+    }
+    const int j = q - (L + 1), pairs = nz - 1 - L;
+    if (j < 2 * pairs) {
+        *type = (j & 1) ? kPhaseA : kPhaseB;
+        *plane = (j & 1) ? (j >> 1) + L : (j >> 1);
+        return;
+    }
+    *type = kPhaseB;
+    *plane = pairs + (j - 2 * pairs);
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int load_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until *ctr >= target; false when the pass was aborted or the wait timed out (then aborts).
+__device__ inline bool fused_wait(const FusedArgs& F, const int* ctr, int target) {
+    if (load_acquire(ctr) >= target) return true;
+    const long long t0 = global_ns();
+    unsigned ns = 32;
+    while (load_acquire(ctr) < target) {
+        if (load_acquire(F.abort)) return false;
+        if (global_ns() - t0 > F.timeout_ns) {
+            atomicExch(F.abort, 1);
+            return false;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns *= 2;
+    }
+    return true;
+}
+
+// Tiles holding the rows y0 - 1 .. y1 + 1 (cyclically) around the rows y0 .. y1 of tile j: the
+// first tile and how many. A cell pulls from (x +- 1, y +- 1), and the x wrap stays in its row.
+__device__ __forceinline__ void tile_window(int j, int tiles, int tile_cells, int nx, int nxy, int* first,
+                                            int* count) {
+    const int c0 = j * tile_cells, c1 = min(c0 + tile_cells, nxy) - 1;
+    const int y0 = c0 / nx, y1 = c1 / nx;
+    const long long span = (long long)(y1 - y0 + 3) * nx;
+    if (span >= nxy) {
+        *first = 0;
+        *count = tiles;
+        return;
+    }
+    int lo = (y0 - 1) * nx;
+    if (lo < 0) lo += nxy;
+    const int hi = lo + (int)span - 1;  // may pass nxy: wraps
+    *first = lo / tile_cells;
+    *count = hi < nxy ? hi / tile_cells - *first + 1 : (tiles - *first) + ((hi - nxy) / tile_cells + 1);
+    if (*count > tiles) *count = tiles;
+}
+
+__device__ __forceinline__ bool plane_has_sources(const FusedArgs& F, int p) {
+    return F.plane_special[p + 1] > F.plane_special[p];
+}
+
+// An item of a pass: phase (type, plane) and j < tiles for a tile, j == tiles for the plane's
+// source cells.
+struct FusedItem {
+    int type, plane, j;
+};
+
+__device__ __forceinline__ FusedItem fused_item(int item, int per_phase, int nz, int L) {
+    FusedItem it;
+    const int q = item / per_phase;
+    it.j = item - q * per_phase;
+    fused_phase(q, nz, L, &it.type, &it.plane);
+    return it;
+}
+
+// Dependencies of item `it`, checked by the 32 lanes of one warp at once: the tile flags of three
+// planes' windows are spread over the lanes, so a satisfied item costs one round of loads. `own`
+// is the item the same block runs just before this one: it is complete by the time this one
+// starts (the block's barriers order it), so it is not waited for. Same verdict in every lane.
+__device__ inline bool fused_ready_warp(const FusedArgs& F, int nz, FusedItem it, FusedItem own, int nx, int nxy,
+                                        bool wait) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    // one look (wait == false) or a bounded wait
+    auto reached = [&](const int* p, int target) { return wait ? fused_wait(F, p, target) : load_acquire(p) >= target; };
+    if (it.j == F.tiles) {  // source-cell item: every tile of its own phase
+        const bool own_tile = own.type == it.type && own.plane == it.plane && own.j < F.tiles;
+        if (lane == 0) ok = reached(F.count + it.type * nz + it.plane, F.tiles - (own_tile ? 1 : 0));
+        return __all_sync(0xffffffffu, ok);
+    }
+    int q[3];
+    int wtype;
+    if (it.type == kPhaseB) {
+        wtype = kPhaseA;
+        q[0] = (it.plane + nz - 1) % nz;
+        q[1] = it.plane;
+        q[2] = (it.plane + 1) % nz;
+    } else {
+        const int prev = it.plane - F.R;  // plane that last used this ring slot
+        if (!(it.plane >= 1 && it.plane <= nz - 2 && prev >= 1)) return true;
+        wtype = kPhaseB;
+        q[0] = prev - 1;
+        q[1] = prev;
+        q[2] = prev + 1;
+    }
+    int first, count;
+    tile_window(it.j, F.tiles, F.tile_cells, nx, nxy, &first, &count);
+    for (int idx = lane; ok && idx < 3 * count; idx += 32) {
+        const int k = idx / count;
+        int t = first + (idx - k * count);
+        if (t >= F.tiles) t -= F.tiles;
+        if (own.type == wtype && own.plane == q[k] && own.j == t) continue;
+        ok = reached(F.tile_flag + ((size_t)wtype * nz + q[k]) * F.tiles + t, F.epoch);
+    }
+    if (ok && lane < 3 && plane_has_sources(F, q[lane]) &&
+        !(own.type == wtype && own.plane == q[lane] && own.j == F.tiles))
+        ok = reached(F.fix_flag + wtype * nz + q[lane], F.epoch);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Publish a finished item (after every store of the block: the caller's barrier orders them).
+__device__ __forceinline__ void fused_publish(const FusedArgs& F, int nz, FusedItem it) {
+    __threadfence();
+    if (it.j < F.tiles) {
+        atomicExch(F.tile_flag + ((size_t)it.type * nz + it.plane) * F.tiles + it.j, F.epoch);
+        atomicAdd(F.count + it.type * nz + it.plane, 1);
+    } else {
+        atomicExch(F.fix_flag + it.type * nz + it.plane, F.epoch);
+    }
+}
+
+// Threads of a two-step block: kBlock compute threads and one scheduler warp.
+constexpr int kFusedThreads = kBlock + 32;
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// The persistent loop. The scheduler warp (threads kBlock ..) takes the next item from the
+// counter and looks at its inputs while the kBlock compute threads run the current one:
+//   compute: bar.sync(handoff) -> read the item -> work -> bar.arrive(done) -> repeat;
+//   scheduler: take item n+1 and look once at its inputs -> bar.sync(done) (item n finished) ->
+//     if they were all there: hand n+1 over (bar.arrive(handoff)), then publish n while it runs;
+//     otherwise: publish n first, then wait for n+1's inputs and hand it over.
+// Publishing never waits behind another item's inputs, so the earliest unpublished item can
+// always proceed (every item waits only for earlier ones); and in the usual case neither the
+// check nor the publication's fence delays the compute threads. Item n+1's dependence on n
+// itself is not looked up: the block's barriers order n before n+1.
+template <class Work>
+__device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, Work&& work) {
+    constexpr int kHandoff = 1, kDone = 2;
+    __shared__ int s_item[2], s_ok[2];
+    const int per_phase = F.tiles + 1;
+    const int total = 2 * nz * per_phase;
+    if (threadIdx.x < kBlock) {
+        for (int buf = 0;; buf ^= 1) {
+            named_sync(kHandoff, kFusedThreads);
+            const int item = s_item[buf];
+            if (item >= total || !s_ok[buf]) return;
+            const FusedItem it = fused_item(item, per_phase, nz, F.L);
+            work(it.type, it.plane, it.j);
+            named_arrive(kDone, kFusedThreads);
+        }
+    }
+    // scheduler warp
+    const int lane = threadIdx.x & 31;
+    const FusedItem none{-1, -1, -1};
+    int item = 0;
+    if (lane == 0) item = atomicAdd(F.next, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    bool ok = item >= total || fused_ready_warp(F, nz, fused_item(item, per_phase, nz, F.L), none, nx, nxy, true);
+    if (lane == 0) {
+        s_item[0] = item;
+        s_ok[0] = ok ? 1 : 0;
+    }
+    named_arrive(kHandoff, kFusedThreads);
+    for (int buf = 1;; buf ^= 1) {
+        if (item >= total || !ok) return;
+        const FusedItem cur = fused_item(item, per_phase, nz, F.L);
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(F.next, 1);
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+        const FusedItem next = nxt < total ? fused_item(nxt, per_phase, nz, F.L) : none;
+        const bool ready = nxt >= total || fused_ready_warp(F, nz, next, cur, nx, nxy, false);
+        named_sync(kDone, kFusedThreads);  // the compute threads finished `cur`
+        bool ok2 = true;
+        if (ready) {
+            if (lane == 0) {
+                s_item[buf] = nxt;
+                s_ok[buf] = 1;
+            }
+            named_arrive(kHandoff, kFusedThreads);
+            if (lane == 0) fused_publish(F, nz, cur);
+        } else {
+            if (lane == 0) fused_publish(F, nz, cur);
+            __syncwarp();
+            ok2 = fused_ready_warp(F, nz, next, none, nx, nxy, true);
+            if (lane == 0) {
+                s_item[buf] = nxt;
+                s_ok[buf] = ok2 ? 1 : 0;
+            }
+            named_arrive(kHandoff, kFusedThreads);
+        }
+        item = nxt;
+        ok = ok2;
+    }
+}
+
 // --- host-side launchers (one set per model) -----------------------------------------------
 // Each returns the number of kernels it enqueued (errors are read with cudaGetLastError).
 int mm_launch_step(const StepArgs& a, cudaStream_t st);
@@ -540,6 +815,13 @@ int hv_batch_occupancy(int storage, int block);
 // first term of loss_plane. record_step: a forward step that also writes the adjoint record of
 // every cell into a.rec.
 int mm_launch_record_step(const StepArgs& a, cudaStream_t st);
+// Two steps in one pass: aA is step t (fin = the current buffer), aB step t + 1 (fout = the other
+// buffer); F describes the ring and the counters (zeroed by the caller). Returns launches.
+int mm_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, cudaStream_t st);
+int hv_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, cudaStream_t st);
+// Resident blocks per SM of the two-step kernel.
+int mm_fused2_occupancy(int storage, int media_mode);
+int hv_fused2_occupancy(int storage, int media_mode);
 int hv_launch_record_step(const StepArgs& a, cudaStream_t st);
 int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
 int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st);

@@ -135,12 +135,24 @@ __device__ __forceinline__ void mm_put(const StepArgs& a, int d, int i, float4 v
     fout[(size_t)d * a.g.n + i] = Pack4<S>::pack(v, a.scale);
 }
 
+// Where a step reads its populations and writes its results: the context's A/B buffers.
+struct MMBuffers {
+    template <int S>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) const {
+        mm_pull<S>(a, h, f);
+    }
+    template <int S>
+    __device__ void put(const StepArgs& a, int d, int i, float4 v) const {
+        mm_put<S>(a, d, i, v);
+    }
+};
+
 // Update of cell i; m is its index in the special-cell list when kSpecial.
-template <int S, int M, bool kSpecial, bool kRho, bool kRecord = false>
-__device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m) {
+template <int S, int M, bool kSpecial, bool kRho, bool kRecord = false, class IO = MMBuffers>
+__device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m, const IO& io = IO{}) {
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 f[12];
-    mm_pull<S>(a, h, f);
+    io.template pull<S>(a, h, f);
     const MatCoef mat = load_coef<kModelMM, M>(a.media, i, a.eps0, a.mu0);
     float rest0 = 0.f;
     if constexpr (kRho) rest0 = a.rho_in[i];
@@ -174,7 +186,7 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m) {
                 o = make_float4(alpha, -alpha, beta, -beta);
             }
         }
-        mm_put<S>(a, d, i, o);
+        io.template put<S>(a, d, i, o);
     });
     if constexpr (kRho) a.rho_out[i] = 2.f * F.rho - rest0;  // f_0^(0)eq = rho_c; stays in place
     if constexpr (kRecord) {  // what the adjoint of this step needs: E and X
@@ -398,6 +410,89 @@ __global__ void __launch_bounds__(kBlock, 3) mm_record_kernel(StepArgs a) {
         if (i >= a.g.n) return;
         mm_update<kF32, M, false, kRho, true>(a, i, 0);
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Two steps per pass (see FusedArgs). Phase A reads the A/B buffer once (streaming loads that L2
+// may evict first) and writes the intermediate plane; phase B pulls from the intermediate planes
+// (L2 loads: they were written by other blocks of this launch) and writes the other A/B buffer
+// once (streaming stores). The arithmetic is mm_update's, so the pair of steps gives the same
+// bits as two single steps.
+template <int S>
+struct MMToRing {
+    using T = typename Pack4<S>::T;
+    T* plane;  // slot of this cell's plane
+    int base;  // first cell of the plane
+    int nxy;
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) const {
+        const T* __restrict__ fin = static_cast<const T*>(a.fin);
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            const int src = shifted<-kMMV[d][0], -kMMV[d][1], -kMMV[d][2]>(h);
+            f[d] = Pack4<S>::unpack(__ldcs(fin + (size_t)d * a.g.n + src), a.inv_scale);
+        });
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int d, int i, float4 v) const {
+        __stcg(plane + (size_t)d * nxy + (i - base), Pack4<S>::pack(v, a.scale));
+    }
+};
+
+template <int S>
+struct MMFromRing {
+    using T = typename Pack4<S>::T;
+    const T* plane[3];  // slots of planes z - 1, z, z + 1
+    int nxy;
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) const {
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int sx = -kMMV[d][0], sy = -kMMV[d][1], sz = -kMMV[d][2];
+            const T* src = plane[sz + 1] + (size_t)d * nxy + h.xo[sx + 1] + h.yo[sy + 1];
+            f[d] = Pack4<S>::unpack(__ldcg(src), a.inv_scale);
+        });
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int d, int i, float4 v) const {
+        T* __restrict__ fout = static_cast<T*>(a.fout);
+        __stcs(fout + (size_t)d * a.g.n + i, Pack4<S>::pack(v, a.scale));
+    }
+};
+
+template <int S, int M>
+__global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA, StepArgs aB, FusedArgs F) {
+    using T = typename Pack4<S>::T;
+    const int nz = aA.g.nz, nxy = aA.g.nx * aA.g.ny;
+    auto slot = [&](int p) -> T* {
+        if (p == 0) return static_cast<T*>(F.lo);
+        if (p == nz - 1) return static_cast<T*>(F.hi);
+        return static_cast<T*>(F.ring) + (size_t)(p % F.R) * 12 * nxy;
+    };
+    fused_loop(F, aA.g.nx, nxy, nz, [&](int type, int p, int j) {
+        const int base = p * nxy;
+        if (type == kPhaseA) {
+            const MMToRing<S> io{slot(p), base, nxy};
+            if (j < F.tiles) {
+                const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
+                for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
+                    mm_update<S, M, false, false, false>(aA, i, 0, io);
+            } else {
+                for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
+                    mm_update<S, M, true, false, false>(aA, aA.sv.cell[m], m, io);
+            }
+        } else {
+            const MMFromRing<S> io{{slot((p + nz - 1) % nz), slot(p), slot((p + 1) % nz)}, nxy};
+            if (j < F.tiles) {
+                const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
+                for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
+                    mm_update<S, M, false, false, false>(aB, i, 0, io);
+            } else {
+                for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
+                    mm_update<S, M, true, false, false>(aB, aB.sv.cell[m], m, io);
+            }
+        }
+    });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -680,6 +775,28 @@ int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t s
     with_media(A.a.media_mode, [&](auto mc) {
         constexpr int M = decltype(mc)::value;
         mm_adjoint_terminal_kernel<M><<<blocks_for(n_plane), kBlock, 0, st>>>(A, n_plane);
+    });
+    return 1;
+}
+
+int mm_fused2_occupancy(int storage, int media_mode) {
+    int blocks = 0;
+    with_storage(storage, [&](auto sc) {
+        with_media(media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mm_fused2_kernel<S, M>, kFusedThreads, 0);
+        });
+    });
+    return blocks;
+}
+
+int mm_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, cudaStream_t st) {
+    const int grid = fused_grid(mm_fused2_occupancy(aA.storage, aA.media_mode));
+    with_storage(aA.storage, [&](auto sc) {
+        with_media(aA.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            mm_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
+        });
     });
     return 1;
 }

@@ -94,6 +94,8 @@ def load_library(path: str | None = None):
         "lbm_destroy": (I, [P]),
         "lbm_adjoint": (I, [P, I, I, I, I, ctypes.POINTER(D), P, P, I]),
         "lbm_adjoint_release": (I, [P]),
+        "lbm_set_step_fusion": (I, [P, I, I]),
+        "lbm_step_fusion_active": (I, [P]),
         "lbm_halo_bytes": (I64, [P]),
         "lbm_halo_pack": (I, [P, I, P, I]),
         "lbm_halo_unpack": (I, [P, I, P, I]),
@@ -290,6 +292,20 @@ class Lattice:
         self._check(self.lib.lbm_adjoint(self.h, int(steps), int(plane_axis), int(plane_index), int(checkpoint_interval),
                                          ctypes.byref(loss), ge.data_ptr(), gs.data_ptr(), 1))
         return loss.value, ge, gs
+
+    # -- two steps per pass ----------------------------------------------------------------------
+    def set_step_fusion(self, mode: int, tile_cells: int = 0) -> None:
+        """0: one launch per step; 1 (default): pairs of steps as one pass when its intermediate
+        planes fit in L2; 2: whenever the lattice allows it. tile_cells: cells per work item of a
+        pass (multiple of 256; 0 keeps the current value) (lbm_set_step_fusion)."""
+        self._check(self.lib.lbm_set_step_fusion(self.h, int(mode), int(tile_cells)))
+
+    @property
+    def step_fusion_active(self) -> bool:
+        rc = int(self.lib.lbm_step_fusion_active(self.h))
+        if rc < 0:
+            self._check(rc)
+        return rc == 1
 
     # -- z-slab halo (z_ghost lattices) ---------------------------------------------------------
     @property

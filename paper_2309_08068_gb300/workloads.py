@@ -145,12 +145,13 @@ def dipole_cells(shape, center, alpha: float = 0.5, r2_max: float = 36.0):
 
 
 def hertz_dipole(model: str, n: int = 256, period: float = 32.0, j0: float = 1e-4, steps: int = 2000,
-                 r2_max: float = 36.0) -> Workload:
+                 r2_max: float = 36.0, nz: int | None = None) -> Workload:
     """Hertz dipole in an n^3 vacuum lattice (Section IV-C source at the benchmark's size): current
     J0 exp(-0.5 |x - x_d|^2) sin(2 pi t / period) z at the centre cell, truncated at |x - x_d|^2 <=
-    r2_max, zero initial fields."""
-    shape = (n, n, n)
-    cells, W = dipole_cells(shape, (n // 2, n // 2, n // 2), r2_max=r2_max)
+    r2_max, zero initial fields. nz, when given, makes the lattice n x n x nz (a thinner copy of the
+    same problem for profiling)."""
+    shape = (n, n, n if nz is None else nz)
+    cells, W = dipole_cells(shape, (n // 2, n // 2, shape[2] // 2), r2_max=r2_max)
     src = Source("current", cells, TimeFunction("sin", j0, period, 0.0), w=W)
     return Workload("hertz_dipole", model, shape, steps, sources=[src])
 

@@ -1,0 +1,126 @@
+"""Two steps per pass (lbm_set_step_fusion): the wavefront kernel must give the populations and
+fields of single steps bit for bit (same arithmetic, intermediate planes in the storage format),
+for both models, every storage and media mode, sources in the wrap-around planes, shallow
+lattices and odd step counts; and it must only switch on where it is allowed."""
+import numpy as np
+import pytest
+
+from helpers import oracle_from_workload, rel_l2
+from paper_2309_08068_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+PLANE = (256, 160)  # 160 tiles of 256 cells per plane: enough to fill the GPU's SMs
+
+
+def run(w, f, steps, mode, tile=0, **kw):
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    L = lattice_from_workload(w, init=False, **kw)
+    L.set_step_fusion(mode, tile)
+    active = L.step_fusion_active
+    L.set_populations(np.asarray(f, np.float32), 0)
+    L.step(steps)
+    out = L.populations_host(), L.fields_host("EBJ"), L.time
+    L.close()
+    return active, out
+
+
+def assert_same(a, b, q):
+    assert np.array_equal(a[0][:q], b[0][:q])
+    for k in a[1]:
+        assert np.array_equal(a[1][k], b[1][k]), k
+    assert a[2] == b[2]
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("media", ["random", "few", "vacuum"])
+@pytest.mark.parametrize("nz", [5, 6, 11])
+def test_fused_pairs_equal_single_steps(model, media, nz):
+    w, f = wl.slab_case(model, PLANE + (nz,), seed=110 + nz, media=media)
+    q = 48 if model == "mm" else 36
+    active, fused = run(w, f, 7, 2)  # three passes and one single step
+    assert active
+    _, single = run(w, f, 7, 0)
+    assert_same(fused, single, q)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("tile", [256, 768, 4096])
+def test_fused_pairs_equal_single_steps_for_every_item_size(model, tile):
+    """Items of 1, 3 and 16 blocks of cells (768 leaves a ragged last item in each plane)."""
+    w, f = wl.slab_case(model, PLANE + (7,), seed=115)
+    q = 48 if model == "mm" else 36
+    active, fused = run(w, f, 4, 2, tile)
+    assert active
+    _, single = run(w, f, 4, 0)
+    assert_same(fused, single, q)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_fused_pairs_equal_single_steps_in_16_bit_storage(model, storage):
+    w, f = wl.slab_case(model, PLANE + (6,), seed=120, amplitude=1e-3)
+    kw = dict(storage=storage, storage_scale=2.0 ** 12 if storage == "f16" else 0.0)
+    q = 48 if model == "mm" else 36
+    active, fused = run(w, f, 6, 2, **kw)
+    assert active
+    _, single = run(w, f, 6, 0, **kw)
+    assert_same(fused, single, q)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_fused_pairs_match_the_oracle(model):
+    w, f = wl.slab_case(model, PLANE + (5,), seed=130)
+    f = np.asarray(f, np.float32).astype(np.float64)
+    for attr in ("eps_r", "mu_r", "sigma"):
+        setattr(w, attr, np.asarray(getattr(w, attr), np.float32).astype(np.float64))
+    for s in w.sources:
+        if s.w is not None:
+            s.w = np.asarray(s.w, np.float32).astype(np.float64)
+        s.E0 = tuple(float(np.float32(v)) for v in s.E0)
+        s.B0 = tuple(float(np.float32(v)) for v in s.B0)
+    _, (pops, _, _) = run(w, f, 4, 2)
+    O = oracle_from_workload(w, init=False, threads=16)
+    O.set_populations(f, 0)
+    O.step(4)
+    q = 48 if model == "mm" else 36
+    assert rel_l2(pops[:q], O.populations()[:q]) <= 1e-5
+
+
+def test_fusion_switches_on_only_where_allowed():
+    from paper_2309_08068_gb300.lbm import Lattice
+    def active(shape, mode=1, **kw):
+        L = Lattice("mm", shape, **kw)
+        L.set_step_fusion(mode)
+        a = L.step_fusion_active
+        L.close()
+        return a
+    assert active(PLANE + (11,))                          # 7 planes of 7.9 MB fit in L2
+    assert not active(PLANE + (11,), mode=0)
+    assert not active(PLANE + (11,), track_rho=True)      # rest populations are not in the ring
+    assert not active(PLANE + (11,), z_ghost=True)        # slabs step one plane range at a time
+    assert not active((64, 64, 11), mode=2)               # 4,096 cells per plane cannot fill the GPU
+    assert not active(PLANE + (3,), mode=2)               # MM runs A 3 planes ahead: nz >= 4
+    assert active(PLANE + (4,), mode=2)
+    assert not active((512, 512, 6))                      # 7 x 50 MB does not fit in L2
+    assert active((512, 512, 6), mode=2)
+
+
+def test_hv_needs_five_planes():
+    from paper_2309_08068_gb300.lbm import Lattice
+    for nz, expect in ((4, False), (5, True)):
+        L = Lattice("hv", PLANE + (nz,))
+        L.set_step_fusion(2)
+        assert L.step_fusion_active == expect
+        L.close()
+
+
+def test_fusion_mode_is_checked():
+    from paper_2309_08068_gb300.lbm import Lattice, LbmError
+    L = Lattice("hv", (8, 8, 8))
+    for mode, tile in ((3, 0), (-1, 0), (1, 100), (1, 8192), (1, -256)):
+        with pytest.raises(LbmError):
+            L.set_step_fusion(mode, tile)
+    L.close()
