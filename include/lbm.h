@@ -226,6 +226,16 @@ int lbm_destroy(lbm_ctx* ctx);
 int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells);
 /* 1 when lbm_step would run pairs of steps as single passes, 0 when not (negative on error). */
 int lbm_step_fusion_active(lbm_ctx* ctx);
+/* Self-check of the two-step pass's work order on the host, with the kernel's own order and tile
+ * window functions, for an nx x ny x nz lattice, ring R, lookahead L and tile_cells per item
+ * (nx * ny <= 2^22). Checks:
+ *   1. every phase appears once;
+ *   2. each phase's waits target earlier phases;
+ *   3. a ring slot is rewritten only after the readers of its previous plane;
+ *   4. a tile's window holds every cell its cells pull from, and windows are symmetric.
+ * Returns 0 when all hold, the number of the first failed check otherwise, LBM_EINVAL for bad
+ * sizes. Needs no GPU. */
+int lbm_fused_schedule_check(int nx, int ny, int nz, int R, int L, int tile_cells);
 
 /* Loss and gradient over the next `steps` time steps (inverse material design; the paper itself
  * only runs forward). From the current populations, the context advances `steps` steps exactly as

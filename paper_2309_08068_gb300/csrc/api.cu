@@ -1816,3 +1816,91 @@ extern "C" int lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper) {
         h.c[h.count++] = HaloChunk{down_src.ptr[k], down_dst.ptr[k], (long long)down_src.bytes[k]};
     return check_launch(lower, launch_halo_copy(h, lower->stream));
 }
+
+// ------------------------------------------------------------------------------------------------
+// lbm_fused_schedule_check: the two-step pass's order and dependency rules, checked on the host
+// with the same functions the kernel uses (fused_phase, tile_window).
+// ------------------------------------------------------------------------------------------------
+extern "C" int lbm_fused_schedule_check(int nx, int ny, int nz, int R, int L, int tile_cells) {
+    if (nx < 1 || ny < 1 || nz < 3 || L < 2 || R < L + 1 || nz < L + 1 || tile_cells < 1) return LBM_EINVAL;
+    const long long nxy_ll = (long long)nx * ny;
+    if (nxy_ll > (1 << 22)) return LBM_EINVAL;
+    const int nxy = (int)nxy_ll, tiles = (nxy + tile_cells - 1) / tile_cells;
+    // 1. the order visits every phase once
+    std::vector<int> posA((size_t)nz, -1), posB((size_t)nz, -1);
+    for (int q = 0; q < 2 * nz; ++q) {
+        int type, plane;
+        fused_phase(q, nz, L, &type, &plane);
+        if (plane < 0 || plane >= nz) return 1;
+        int& slot = type == kPhaseA ? posA[(size_t)plane] : posB[(size_t)plane];
+        if (slot != -1) return 2;
+        slot = q;
+    }
+    for (int p = 0; p < nz; ++p)
+        if (posA[(size_t)p] < 0 || posB[(size_t)p] < 0) return 3;
+    // 2. every wait (the kernel's own rule, fused_waits_on) targets an earlier phase; B(p) covers
+    //    the three planes it reads
+    for (int type = kPhaseA; type <= kPhaseB; ++type)
+        for (int p = 0; p < nz; ++p) {
+            int wtype = 0, q[3];
+            const int nq = fused_waits_on(type, p, nz, R, &wtype, q);
+            const int me = type == kPhaseA ? posA[(size_t)p] : posB[(size_t)p];
+            for (int k = 0; k < nq; ++k) {
+                if (q[k] < 0 || q[k] >= nz) return 4;
+                if ((wtype == kPhaseA ? posA[(size_t)q[k]] : posB[(size_t)q[k]]) >= me) return 4;
+            }
+            if (type == kPhaseB) {
+                bool reads[3] = {false, false, false};
+                for (int k = 0; k < nq; ++k)
+                    for (int d = -1; d <= 1; ++d)
+                        if (wtype == kPhaseA && q[k] == (p + d + nz) % nz) reads[d + 1] = true;
+                if (!(reads[0] && reads[1] && reads[2])) return 5;
+            }
+        }
+    // 3. ring slots: when planes a < b share a slot (both in 1 .. nz - 2, a = b - R m), every B
+    //    phase that reads a is ordered before A(b) through the chain of waits
+    std::vector<std::vector<char>> before((size_t)(2 * nz), std::vector<char>((size_t)(2 * nz), 0));
+    auto id = [&](int type, int p) { return (size_t)(type * nz + p); };
+    std::vector<std::pair<int, int>> order((size_t)(2 * nz));
+    for (int q = 0; q < 2 * nz; ++q) fused_phase(q, nz, L, &order[(size_t)q].first, &order[(size_t)q].second);
+    for (int qi = 0; qi < 2 * nz; ++qi) {  // closure of the waits, in order (waits point backwards)
+        const int type = order[(size_t)qi].first, p = order[(size_t)qi].second;
+        int wtype = 0, q[3];
+        const int nq = fused_waits_on(type, p, nz, R, &wtype, q);
+        std::vector<char>& mine = before[id(type, p)];
+        for (int k = 0; k < nq; ++k) {
+            mine[id(wtype, q[k])] = 1;
+            const std::vector<char>& theirs = before[id(wtype, q[k])];
+            for (size_t z = 0; z < theirs.size(); ++z) mine[z] |= theirs[z];
+        }
+    }
+    for (int b = 1; b <= nz - 2; ++b)
+        for (int a = b - R; a >= 1; a -= R)
+            for (int d = -1; d <= 1; ++d)
+                if (!before[id(kPhaseA, b)][id(kPhaseB, (a + d + nz) % nz)]) return 6;
+    // 4. tile windows: every cell a tile's cells pull from (x +- 1, y +- 1, periodic) lies in a tile
+    //    of the window, and the window relation is symmetric (needed by the slot reuse waits)
+    std::vector<char> in_window((size_t)tiles);
+    std::vector<std::vector<char>> win((size_t)tiles);
+    for (int j = 0; j < tiles; ++j) {
+        int first, count;
+        tile_window(j, tiles, tile_cells, nx, nxy, &first, &count);
+        if (count < 1 || count > tiles || first < 0 || first >= tiles) return 7;
+        std::fill(in_window.begin(), in_window.end(), 0);
+        for (int k = 0, t = first; k < count; ++k, t = (t + 1) % tiles) in_window[(size_t)t] = 1;
+        win[(size_t)j] = in_window;
+        const int c1 = std::min((j + 1) * tile_cells, nxy);
+        for (int c = j * tile_cells; c < c1; ++c) {
+            const int x = c % nx, y = c / nx;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int cc = (x + dx + nx) % nx + nx * ((y + dy + ny) % ny);
+                    if (!in_window[(size_t)(cc / tile_cells)]) return 8;
+                }
+        }
+    }
+    for (int a = 0; a < tiles; ++a)
+        for (int b = 0; b < tiles; ++b)
+            if (win[(size_t)a][(size_t)b] != win[(size_t)b][(size_t)a]) return 9;
+    return LBM_OK;
+}

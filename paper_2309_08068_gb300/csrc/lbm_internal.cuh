@@ -546,7 +546,7 @@ struct FusedArgs {
 
 enum { kPhaseA = 0, kPhaseB = 1 };
 
-__device__ __forceinline__ void fused_phase(int q, int nz, int L, int* type, int* plane) {
+__host__ __device__ __forceinline__ void fused_phase(int q, int nz, int L, int* type, int* plane) {
     if (q < L + 1) {
         *type = kPhaseA;
         *plane = q == 0 ? nz - 1 : q - 1;
@@ -593,9 +593,9 @@ __device__ inline bool fused_wait(const FusedArgs& F, const int* ctr, int target
 
 // Tiles holding the rows y0 - 1 .. y1 + 1 (cyclically) around the rows y0 .. y1 of tile j: the
 // first tile and how many. A cell pulls from (x +- 1, y +- 1), and the x wrap stays in its row.
-__device__ __forceinline__ void tile_window(int j, int tiles, int tile_cells, int nx, int nxy, int* first,
-                                            int* count) {
-    const int c0 = j * tile_cells, c1 = min(c0 + tile_cells, nxy) - 1;
+__host__ __device__ __forceinline__ void tile_window(int j, int tiles, int tile_cells, int nx, int nxy, int* first,
+                                                     int* count) {
+    const int c0 = j * tile_cells, c1 = (c0 + tile_cells < nxy ? c0 + tile_cells : nxy) - 1;
     const int y0 = c0 / nx, y1 = c1 / nx;
     const long long span = (long long)(y1 - y0 + 3) * nx;
     if (span >= nxy) {
@@ -609,6 +609,27 @@ __device__ __forceinline__ void tile_window(int j, int tiles, int tile_cells, in
     *first = lo / tile_cells;
     *count = hi < nxy ? hi / tile_cells - *first + 1 : (tiles - *first) + ((hi - nxy) / tile_cells + 1);
     if (*count > tiles) *count = tiles;
+}
+
+// The phases a tile of phase (type, plane) waits for: the tiles of planes q[0..2] in phase *wtype
+// within its window. B(p) reads the intermediate planes p - 1, p, p + 1 written by A; A(p) rewrites
+// the ring slot whose previous plane, p - R, the B phases p - R - 1 .. p - R + 1 read. Returns the
+// number of planes (0: nothing to wait for).
+__host__ __device__ __forceinline__ int fused_waits_on(int type, int plane, int nz, int R, int* wtype, int* q) {
+    if (type == kPhaseB) {
+        *wtype = kPhaseA;
+        q[0] = (plane + nz - 1) % nz;
+        q[1] = plane;
+        q[2] = (plane + 1) % nz;
+        return 3;
+    }
+    const int prev = plane - R;
+    if (!(plane >= 1 && plane <= nz - 2 && prev >= 1)) return 0;
+    *wtype = kPhaseB;
+    q[0] = prev - 1;
+    q[1] = prev;
+    q[2] = prev + 1;
+    return 3;
 }
 
 __device__ __forceinline__ bool plane_has_sources(const FusedArgs& F, int p) {
@@ -645,20 +666,8 @@ __device__ inline bool fused_ready_warp(const FusedArgs& F, int nz, FusedItem it
         return __all_sync(0xffffffffu, ok);
     }
     int q[3];
-    int wtype;
-    if (it.type == kPhaseB) {
-        wtype = kPhaseA;
-        q[0] = (it.plane + nz - 1) % nz;
-        q[1] = it.plane;
-        q[2] = (it.plane + 1) % nz;
-    } else {
-        const int prev = it.plane - F.R;  // plane that last used this ring slot
-        if (!(it.plane >= 1 && it.plane <= nz - 2 && prev >= 1)) return true;
-        wtype = kPhaseB;
-        q[0] = prev - 1;
-        q[1] = prev;
-        q[2] = prev + 1;
-    }
+    int wtype = 0;
+    if (fused_waits_on(it.type, it.plane, nz, F.R, &wtype, q) == 0) return true;
     int first, count;
     tile_window(it.j, F.tiles, F.tile_cells, nx, nxy, &first, &count);
     for (int idx = lane; ok && idx < 3 * count; idx += 32) {

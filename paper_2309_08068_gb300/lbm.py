@@ -96,6 +96,7 @@ def load_library(path: str | None = None):
         "lbm_adjoint_release": (I, [P]),
         "lbm_set_step_fusion": (I, [P, I, I]),
         "lbm_step_fusion_active": (I, [P]),
+        "lbm_fused_schedule_check": (I, [I, I, I, I, I, I]),
         "lbm_halo_bytes": (I64, [P]),
         "lbm_halo_pack": (I, [P, I, P, I]),
         "lbm_halo_unpack": (I, [P, I, P, I]),
