@@ -224,25 +224,6 @@ int lbm_destroy(lbm_ctx* ctx);
  * tile_cells: cells per work item of a pass, a multiple of 256 up to 4096; 0 keeps the current
  * value (default 256 for MM, 512 for HV, the fastest on GB300). */
 int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells);
-/* Shape of the two-step pass. Every shape gives the same bits; the defaults are the fastest
- * measured on GB300.
- *   ring: intermediate ring slots R (0: the model's default, 5 for MM, 6 for HV); lookahead: phases
- *   A run L planes ahead of phases B (0: default, 3 for MM, 4 for HV). Needs L >= 2, R >= L + 1,
- *   R <= 64.
- *   staged: 1 stages each work item's inputs in shared memory: where an item is whole plane rows
- *   whose inputs fit in 56 KB (one row of 256 cells: 48 KB for MM, 36 KB for HV, in FP32) and every
- *   row starts on a 16-byte boundary, the scheduler warp copies the rows the item pulls from with
- *   bulk asynchronous copies, two items in flight. 0: the compute threads load their inputs from
- *   global memory. -1: the default.
- *   discard: 1 lets a finished phase-B tile invalidate the L2 lines of the intermediate values it
- *   read (no write-back) when items are whole rows of whole 128-byte lines and hold no source cell;
- *   0 (default) does not.
- * Staging changes the item size to whole rows unless lbm_set_step_fusion fixed it; the next pass
- * then reallocates its counters. Errors: LBM_EINVAL for values out of range. */
-int lbm_set_pass_shape(lbm_ctx* ctx, int ring, int lookahead, int staged, int discard);
-/* 1 when lbm_step would run pairs of steps as staged passes (lbm_set_pass_shape), 0 when not
- * (negative on error). */
-int lbm_pass_staged(lbm_ctx* ctx);
 /* 1 when lbm_step would run pairs of steps as single passes, 0 when not (negative on error). */
 int lbm_step_fusion_active(lbm_ctx* ctx);
 /* Self-check of the two-step pass's work order on the host, with the kernel's own order and tile

@@ -86,11 +86,6 @@ struct lbm_ctx {
     int fused_epoch = 0;           // number of the last pass launched
     int* d_plane_special = nullptr;
     int plane_special_version = -1;
-    unsigned char* d_tile_special = nullptr;  // nz x tiles: 1 where a pass's tile holds source cells
-    int tile_special_version = -1;
-    int pass_R = 0, pass_L = 0;    // ring slots and lookahead of a pass (0: the model's default)
-    int pass_staged = -1;          // stage tile inputs in shared memory: -1 default, 0 off, 1 on
-    int pass_discard = 0;          // B tiles invalidate the intermediate lines they read
     int sources_version = 0;
     int fused_pending = 0;         // a pass ran since the abort flag was last read
     std::vector<int> h_cell;       // host copy of the special-cell list (sorted)
@@ -222,38 +217,9 @@ static_assert(kFusedMM.L >= 2 && kFusedMM.R >= kFusedMM.L + 1 && kFusedHV.L >= 2
               "the pass order needs R >= L + 1 >= 3");
 constexpr long long kFusedTimeoutNs = 2000000000;  // a dependency wait longer than this aborts
 
-FusedShape fused_shape(const lbm_ctx* c) {
-    FusedShape f = c->model == LBM_MM ? kFusedMM : kFusedHV;
-    if (c->pass_L) f.L = c->pass_L;
-    if (c->pass_R) f.R = c->pass_R;
-    return f;
-}
+FusedShape fused_shape(const lbm_ctx* c) { return c->model == LBM_MM ? kFusedMM : kFusedHV; }
 
-// Bytes of all directions' populations of one cell (MM: 12 groups; HV: 6 groups and 6 pairs).
-size_t cell_pop_bytes(const lbm_ctx* c) {
-    return group_bytes(c->model, c->storage) + (c->model == LBM_HV ? pair_bytes(c->storage) : 0);
-}
-
-// The staged pass: tiles of whole rows whose inputs (two stages) fit in shared memory, and rows of
-// every population array that start and end on 16-byte boundaries (bulk copies need both).
-constexpr bool kStagedByDefault = false;
-constexpr size_t kStageCap = 56 * 1024;  // bytes per stage
-int staged_tile_default(const lbm_ctx* c) { return c->g.nx * std::max(1, (kBlock + c->g.nx - 1) / c->g.nx); }
-bool staged_fits(const lbm_ctx* c, int tile) {
-    const bool on = c->pass_staged < 0 ? kStagedByDefault : c->pass_staged != 0;
-    if (!on || tile % c->g.nx != 0 || (size_t)tile * cell_pop_bytes(c) > kStageCap) return false;
-    const size_t nx = (size_t)c->g.nx;
-    if (c->model == LBM_MM) return nx * (group_bytes(c->model, c->storage) / 12) % 16 == 0;
-    return nx * (group_bytes(c->model, c->storage) / 6) % 16 == 0 && nx * (pair_bytes(c->storage) / 6) % 16 == 0;
-}
-
-int fused_tile_cells(const lbm_ctx* c) {
-    if (c->fused_tile) return c->fused_tile;
-    if (staged_fits(c, staged_tile_default(c))) return staged_tile_default(c);
-    return fused_shape(c).tile;
-}
-bool fused_staged(const lbm_ctx* c) { return staged_fits(c, fused_tile_cells(c)); }
-int fused_stage_bytes(const lbm_ctx* c) { return (int)((size_t)fused_tile_cells(c) * cell_pop_bytes(c)); }
+int fused_tile_cells(const lbm_ctx* c) { return c->fused_tile ? c->fused_tile : fused_shape(c).tile; }
 int fused_tiles(const lbm_ctx* c) { return (c->g.nx * c->g.ny + fused_tile_cells(c) - 1) / fused_tile_cells(c); }
 
 // Pass control block: [item counter][2 nz tile counters][abort][2 nz source-item flags]
@@ -323,29 +289,7 @@ int ensure_fused(lbm_ctx* c) {
         CUDA_TRY(c, cudaMemcpy(c->d_plane_special, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
         c->plane_special_version = c->sources_version;
     }
-    if (c->tile_special_version != c->sources_version || !c->d_tile_special) {
-        // tiles that hold source cells keep the intermediate values they read (the plane's source
-        // item pulls them again)
-        const size_t nxy = (size_t)c->g.nx * c->g.ny, tiles = (size_t)fused_tiles(c), cells = fused_tile_cells(c);
-        std::vector<unsigned char> has((size_t)c->g.nz * tiles, 0);
-        for (int cell : c->h_cell) has[(size_t)cell / nxy * tiles + ((size_t)cell % nxy) / cells] = 1;
-        if (!c->d_tile_special && cudaMalloc(&c->d_tile_special, has.size()) != cudaSuccess) {
-            cudaGetLastError();
-            c->d_tile_special = nullptr;
-            return fail(c, LBM_ENOMEM, "lbm_step: cannot allocate the tile source flags");
-        }
-        CUDA_TRY(c, cudaMemcpy(c->d_tile_special, has.data(), has.size(), cudaMemcpyHostToDevice));
-        c->tile_special_version = c->sources_version;
-    }
     return LBM_OK;
-}
-
-// A finished B tile may invalidate the intermediate lines it read when tiles are whole rows and a
-// row of every direction's array is a whole number of 128-byte lines (no other tile reads them).
-bool fused_discard_allowed(const lbm_ctx* c) {
-    const size_t nx = (size_t)c->g.nx;
-    const size_t dir = c->model == LBM_MM ? group_bytes(c->model, c->storage) / 12 : pair_bytes(c->storage) / 6;
-    return c->pass_discard && fused_tile_cells(c) % c->g.nx == 0 && nx * dir % 128 == 0;
 }
 
 int fused_pass(lbm_ctx* c) {
@@ -385,18 +329,9 @@ int fused_pass(lbm_ctx* c) {
     F.fix_flag = c->fused_ctrl + 2 + 2 * nz;
     F.tile_flag = c->fused_ctrl + 2 + 4 * nz;
     F.plane_special = c->d_plane_special;
-    F.tile_special = c->d_tile_special;
-    F.discard = fused_discard_allowed(c) ? 1 : 0;
     F.timeout_ns = kFusedTimeoutNs;
     CUDA_TRY(c, cudaMemsetAsync(c->fused_ctrl, 0, sizeof(int) * (1 + 2 * (size_t)nz), c->stream));
-    int launched;
-    if (fused_staged(c)) {
-        const int sb = fused_stage_bytes(c);
-        launched = c->model == LBM_MM ? mm_launch_fused2s(aA, aB, F, sb, c->stream)
-                                      : hv_launch_fused2s(aA, aB, F, sb, c->stream);
-    } else {
-        launched = c->model == LBM_MM ? mm_launch_fused2(aA, aB, F, c->stream) : hv_launch_fused2(aA, aB, F, c->stream);
-    }
+    const int launched = c->model == LBM_MM ? mm_launch_fused2(aA, aB, F, c->stream) : hv_launch_fused2(aA, aB, F, c->stream);
     int rc = check_launch(c, launched);
     if (rc != LBM_OK) return rc;
     c->fused_pending = 1;
@@ -618,7 +553,6 @@ void release(lbm_ctx* c) {
     c->fused_planes_bytes = 0;
     free_dev(c->fused_ctrl);
     free_dev(c->d_plane_special);
-    free_dev(c->d_tile_special);
 }
 
 // Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
@@ -1003,42 +937,11 @@ int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells) {
     if (tile_cells != 0 && tile_cells != fused_tile_cells(ctx)) {
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
         else cudaDeviceSynchronize();
-        free_dev(ctx->fused_ctrl);      // its flag array depends on the tile count
-        free_dev(ctx->d_tile_special);  // so does the tiles' source map
+        free_dev(ctx->fused_ctrl);  // its flag array depends on the tile count
         ctx->fused_tile = tile_cells;
     }
     ctx->fusion = mode;
     return LBM_OK;
-}
-
-int lbm_set_pass_shape(lbm_ctx* ctx, int ring, int lookahead, int staged, int discard) {
-    if (!ctx) return LBM_EINVAL;
-    const FusedShape def = ctx->model == LBM_MM ? kFusedMM : kFusedHV;
-    const int L = lookahead ? lookahead : def.L, R = ring ? ring : std::max(def.R, L + 1);
-    if (ring < 0 || lookahead < 0 || L < 2 || R < L + 1 || R > 64 || staged < -1 || staged > 1 || discard < 0 ||
-        discard > 1)
-        return fail(ctx, LBM_EINVAL,
-                    "lbm_set_pass_shape: need lookahead 0 or >= 2, ring 0 or lookahead + 1 .. 64, staged -1..1, "
-                    "discard 0..1");
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    else cudaDeviceSynchronize();
-    const int tile_before = fused_tile_cells(ctx);
-    ctx->pass_L = lookahead;
-    ctx->pass_R = R == def.R ? 0 : R;
-    ctx->pass_staged = staged;
-    ctx->pass_discard = discard;
-    if (fused_tile_cells(ctx) != tile_before) {
-        free_dev(ctx->fused_ctrl);  // the flag array and the tiles' source map depend on the tile count
-        free_dev(ctx->d_tile_special);
-    }
-    return LBM_OK;
-}
-
-int lbm_pass_staged(lbm_ctx* ctx) {
-    if (!ctx) return LBM_EINVAL;
-    int rc;
-    if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
-    return fusion_eligible(ctx) && fused_staged(ctx) ? 1 : 0;
 }
 
 int lbm_step_fusion_active(lbm_ctx* ctx) {

@@ -274,149 +274,6 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
     });
 }
 
-// The staged pass (fused_staged_loop): a tile cell pulls from the rows staged in shared memory,
-// direction k at stage[k][r][x - v_kx] for the 4-vectors, then the same for the 2-vectors (r: the
-// cell's row within the tile, x wraps within the row); phase A writes the intermediate slots,
-// phase B the other A/B buffers, as in HVToRing / HVFromRing.
-template <int S, bool kToRing>
-struct HVStaged {
-    using T4 = typename Pack4<S>::T;
-    using T2 = typename Pack2<S>::T;
-    const T4* stage;
-    const T2* stage2;
-    int x, r, rows, nx;
-    T4* out;  // phase A: the slots of the cell's plane
-    T2* out2;
-    int base;  // phase A: the plane's first cell
-    int nxy;
-    template <int S2>
-    __device__ void pull(const StepArgs& a, const Neighbourhood&, float4 (&e)[6], float2 (&hy)[6]) const {
-        static_for<0, 6>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            constexpr int vx = kHVAxis[k] == 0 ? kHVSign[k] : 0;
-            int xs = x - vx;
-            if constexpr (vx > 0) {
-                if (xs < 0) xs += nx;
-            } else if constexpr (vx < 0) {
-                if (xs >= nx) xs -= nx;
-            }
-            const int o = (k * rows + r) * nx + xs;
-            e[k] = Pack4<S>::unpack(stage[o], a.inv_scale);
-            hy[k] = Pack2<S>::unpack(stage2[o], a.inv_scale);
-        });
-    }
-    template <int S2>
-    __device__ void put(const StepArgs& a, int k, int i, float4 e, float2 hy) const {
-        if constexpr (kToRing) {
-            __stcg(out + (size_t)k * nxy + (i - base), Pack4<S>::pack(e, a.scale));
-            __stcg(out2 + (size_t)k * nxy + (i - base), Pack2<S>::pack(hy, a.scale));
-        } else {
-            T4* __restrict__ eout = static_cast<T4*>(a.fout);
-            T2* __restrict__ hout = static_cast<T2*>(a.fout2);
-            __stcs(eout + (size_t)k * a.g.n + i, Pack4<S>::pack(e, a.scale));
-            __stcs(hout + (size_t)k * a.g.n + i, Pack2<S>::pack(hy, a.scale));
-        }
-    }
-};
-
-template <int S, int M>
-__global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2s_kernel(StepArgs aA, StepArgs aB, FusedArgs F,
-                                                                       int stage_bytes) {
-    using T4 = typename Pack4<S>::T;
-    using T2 = typename Pack2<S>::T;
-    extern __shared__ __align__(128) unsigned char stages[];
-    const int nx = aA.g.nx, ny = aA.g.ny, nz = aA.g.nz, nxy = nx * ny;
-    const int rows = F.tile_cells / nx;  // rows per tile
-    const size_t part2 = (size_t)6 * rows * nx * sizeof(T4);  // offset of the 2-vectors in a stage
-    auto slot = [&](int p) -> T4* {
-        if (p == 0) return static_cast<T4*>(F.lo);
-        if (p == nz - 1) return static_cast<T4*>(F.hi);
-        return static_cast<T4*>(F.ring) + (size_t)(p % F.R) * 6 * nxy;
-    };
-    auto slot2 = [&](int p) -> T2* {
-        if (p == 0) return static_cast<T2*>(F.lo2);
-        if (p == nz - 1) return static_cast<T2*>(F.hi2);
-        return static_cast<T2*>(F.ring2) + (size_t)(p % F.R) * 6 * nxy;
-    };
-    auto describe = [&](const FusedItem& it, StagedItem& d) {
-        const int pm = (it.plane + nz - 1) % nz, pp = (it.plane + 1) % nz;
-        d.out[0] = slot(it.plane);
-        d.out[1] = slot2(it.plane);
-        d.in[0][0] = slot(pm);
-        d.in[0][1] = slot(it.plane);
-        d.in[0][2] = slot(pp);
-        d.in[1][0] = slot2(pm);
-        d.in[1][1] = slot2(it.plane);
-        d.in[1][2] = slot2(pp);
-    };
-    // lane k < 6 copies the 4-vectors of direction k, lane 6 + k its 2-vectors: rows y0 - v_ky ..
-    // of plane p - v_kz, from the A/B buffers in phase A, from the intermediate slots in phase B
-    auto copies = [&](const StagedItem& d, unsigned char* stage, int lane, RowCopy& rc) {
-        if (lane >= 12) return false;
-        const int y0 = d.j * rows, nrows = min(rows, ny - y0);
-        static_for<0, 12>([&](auto lc) {
-            constexpr int l = decltype(lc)::value, k = l % 6, arr = l / 6;
-            if (lane == l) {
-                constexpr int vy = kHVAxis[k] == 1 ? kHVSign[k] : 0, vz = kHVAxis[k] == 2 ? kHVSign[k] : 0;
-                const int q = (d.plane - vz + nz) % nz;
-                const size_t elem = arr == 0 ? sizeof(T4) : sizeof(T2);
-                const unsigned char* plane;
-                if (d.type == kPhaseA) {
-                    const void* fin = arr == 0 ? aA.fin : aA.fin2;
-                    plane = static_cast<const unsigned char*>(fin) + ((size_t)k * aA.g.n + (size_t)q * nxy) * elem;
-                } else {
-                    plane = static_cast<const unsigned char*>(d.in[arr][1 - vz]) + (size_t)k * nxy * elem;
-                }
-                unsigned char* dst = stage + (arr == 0 ? 0 : part2) + (size_t)k * rows * nx * elem;
-                rc = RowCopy(dst, plane, y0 - vy, nrows, ny, (uint32_t)(nx * elem));
-            }
-        });
-        return true;
-    };
-    auto work = [&](const StagedItem& d, const unsigned char* stage) {
-        const int p = d.plane, base = p * nxy;
-        if (d.j < F.tiles) {
-            const T4* st = reinterpret_cast<const T4*>(stage);
-            const T2* st2 = reinterpret_cast<const T2*>(stage + part2);
-            const int y0 = d.j * rows, ncell = min(rows, ny - y0) * nx, first = base + y0 * nx;
-            for (int c = threadIdx.x; c < ncell; c += kBlock) {
-                const int r = rows == 1 ? 0 : (int)(((unsigned long long)(unsigned)c * aA.g.mx) >> (32 + aA.g.kx));
-                const int x = c - r * nx;
-                if (d.type == kPhaseA)
-                    hv_update<S, M, false, false>(aA, first + c, 0,
-                                                  HVStaged<S, true>{st, st2, x, r, rows, nx, static_cast<T4*>(d.out[0]),
-                                                                    static_cast<T2*>(d.out[1]), base, nxy});
-                else
-                    hv_update<S, M, false, false>(
-                        aB, first + c, 0, HVStaged<S, false>{st, st2, x, r, rows, nx, nullptr, nullptr, base, nxy});
-            }
-        } else if (d.type == kPhaseA) {
-            const HVToRing<S> io{static_cast<T4*>(d.out[0]), static_cast<T2*>(d.out[1]), base, nxy};
-            for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
-                hv_update<S, M, true, false>(aA, aA.sv.cell[m], m, io);
-        } else {
-            const HVFromRing<S> io{{static_cast<const T4*>(d.in[0][0]), static_cast<const T4*>(d.in[0][1]),
-                                    static_cast<const T4*>(d.in[0][2])},
-                                   {static_cast<const T2*>(d.in[1][0]), static_cast<const T2*>(d.in[1][1]),
-                                    static_cast<const T2*>(d.in[1][2])},
-                                   nxy};
-            for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
-                hv_update<S, M, true, false>(aB, aB.sv.cell[m], m, io);
-        }
-    };
-    // the intermediate rows a B tile pulled: direction k from rows y - v_ky of plane p - v_kz
-    auto retire = [&](const StagedItem& d, int lane) {
-        const int y0 = d.j * rows, nrows = min(rows, ny - y0);
-        static_for<0, 6>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            constexpr int vy = kHVAxis[k] == 1 ? kHVSign[k] : 0, vz = kHVAxis[k] == 2 ? kHVSign[k] : 0;
-            retire_rows<vy>(static_cast<const T4*>(d.in[0][1 - vz]) + (size_t)k * nxy, y0, nrows, nx, ny, lane);
-            retire_rows<vy>(static_cast<const T2*>(d.in[1][1 - vz]) + (size_t)k * nxy, y0, nrows, nx, ny, lane);
-        });
-    };
-    fused_staged_loop(F, nx, nxy, nz, stages, stage_bytes, describe, copies, work, retire);
-}
-
 template <int S, int M, bool kSpecial>
 __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
     if constexpr (kSpecial) {
@@ -868,39 +725,6 @@ int hv_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F,
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             hv_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
-        });
-    });
-    return 1;
-}
-
-template <int S, int M>
-void hv_fused2s_smem(int stage_bytes) {
-    static int set = 0;  // the largest dynamic shared memory allowed so far (per instantiation)
-    if (2 * stage_bytes > set) {
-        cudaFuncSetAttribute(hv_fused2s_kernel<S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage_bytes);
-        set = 2 * stage_bytes;
-    }
-}
-
-int hv_fused2s_occupancy(int storage, int media_mode, int stage_bytes) {
-    int blocks = 0;
-    with_storage(storage, [&](auto sc) {
-        with_media(media_mode, [&](auto mc) {
-            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
-            hv_fused2s_smem<S, M>(stage_bytes);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, hv_fused2s_kernel<S, M>, kFusedThreads,
-                                                          2 * (size_t)stage_bytes);
-        });
-    });
-    return blocks;
-}
-
-int hv_launch_fused2s(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, int stage_bytes, cudaStream_t st) {
-    const int grid = fused_grid(hv_fused2s_occupancy(aA.storage, aA.media_mode, stage_bytes));
-    with_storage(aA.storage, [&](auto sc) {
-        with_media(aA.media_mode, [&](auto mc) {
-            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
-            hv_fused2s_kernel<S, M><<<grid, kFusedThreads, 2 * (size_t)stage_bytes, st>>>(aA, aB, F, stage_bytes);
         });
     });
     return 1;

@@ -541,8 +541,6 @@ struct FusedArgs {
     int* fix_flag;              // 2 nz source-cell item flags, A then B
     int* abort;                 // set when a wait timed out
     const int* plane_special;   // nz + 1 offsets of each plane's cells in the special-cell list
-    const unsigned char* tile_special;  // nz x tiles: 1 where a tile holds source cells
-    int discard;                // 1: a finished B tile invalidates the intermediate lines it read
     long long timeout_ns;
 };
 
@@ -776,298 +774,6 @@ __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, W
     }
 }
 
-// --- mbarriers (shared memory, CTA scope) -------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-// Arrive (release at CTA scope).
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b)) : "memory");
-}
-// Has the phase of parity `par` completed? (acquire at CTA scope). test_wait answers at once;
-// try_wait may first suspend the thread for a while.
-__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned par) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(smem_u32(b)), "r"(par)
-                 : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned par) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(smem_u32(b)), "r"(par)
-                 : "memory");
-    return ok != 0;
-}
-
-// --- retiring the intermediate values a B tile has read ----------------------------------------
-// In a pull step every stored value is read by exactly one cell: value d of cell x by cell x + v_d.
-// So once a tile of B(p) has read its inputs, the intermediate values it pulled are dead. Left in
-// L2 they are dirty lines, which L2 writes back to HBM when it evicts them. A finished tile may
-// therefore invalidate them (discard.global.L2: the line is dropped without a write-back and its
-// contents become undefined), when
-//   * tiles are whole rows and a row of one direction's array is a whole number of 128-byte lines
-//     (the host sets F.discard only then), so the lines a tile read are read by no other tile;
-//   * the tile holds no source cell: the plane's source item recomputes those cells later and
-//     pulls the same values again;
-//   * the lines are invalidated after the tile's inputs were read and before the tile is
-//     published (the A phase that rewrites the slot waits for that).
-__device__ __forceinline__ bool fused_retires(const FusedArgs& F, FusedItem it) {
-    return F.discard && it.type == kPhaseB && it.j < F.tiles && !F.tile_special[(size_t)it.plane * F.tiles + it.j];
-}
-
-__device__ __forceinline__ void discard_line(const void* p) {
-    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
-}
-
-// Invalidate, over the 32 lanes of a warp, rows y0 - VY .. y0 - VY + rows - 1 (periodic in y) of
-// one direction's array `dir` of an intermediate plane.
-template <int VY, class T>
-__device__ __forceinline__ void retire_rows(const T* dir, int y0, int rows, int nx, int ny, int lane) {
-    const int lines = nx * (int)sizeof(T) / 128;  // per row
-    for (int r = lane; r < rows * lines; r += 32) {
-        const int row = r / lines, line = r - row * lines;
-        int y = y0 + row - VY;
-        if (y < 0) y += ny;
-        else if (y >= ny) y -= ny;
-        discard_line(reinterpret_cast<const char*>(dir + (size_t)y * nx) + (size_t)line * 128);
-    }
-}
-
-// --- two steps per pass, each item's inputs staged in shared memory ----------------------------
-// The same pass as fused_loop (order, dependencies, flags), for tiles of whole rows. Instead of
-// each compute thread loading its 48 (MM) or 36 (HV) values from HBM or L2, the scheduler warp
-// copies the rows a tile pulls from, one block of rows per direction, into shared memory with
-// bulk asynchronous copies (cp.async.bulk) that complete on an mbarrier. Two stages alternate:
-// while the compute warps work on one item, the copies of the next one are in flight.
-//   * Phase A inputs are the previous pass's populations, which nothing in the pass writes: their
-//     copies start as soon as the stage is free, before the slot-reuse wait.
-//   * Phase B inputs are intermediate rows: their copies start once the A tiles that write them
-//     are published.
-//   * Source-cell items carry no copies; their compute threads load from global memory as in
-//     fused_loop.
-// Direction k of a tile with rows y0 .. y0 + rows - 1 pulls from rows y0 - v_ky .. of plane
-// p - v_kz, so the stage holds, per direction, `rows` consecutive rows (periodic in y); the x shift
-// is taken in shared memory, where the whole row is present.
-// Barriers per stage: `full` (one arrival by the scheduler, plus the bytes of the copies) and
-// `empty` (one arrival per compute warp). A stage is refilled only after its item is published.
-struct StagedItem {
-    int item;               // -1: the loop ends
-    int type, plane, j;
-    void* out[2];           // phase A: slot of `plane` (groups; HV pairs)
-    const void* in[2][3];   // phase B: slots of planes p - 1, p, p + 1 (groups; HV pairs)
-};
-
-__device__ __forceinline__ uint64_t l2_evict_first() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-// Global -> shared bulk copy (addresses and size multiples of 16 bytes), completing on `bar`.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
-// One direction's rows ystart .. ystart + rows - 1 (ystart in -1 .. ny, periodic) of a plane array
-// whose row 0 is at `plane`: one copy, or two when the rows wrap past ny - 1.
-struct RowCopy {
-    const unsigned char* src[2];
-    unsigned char* dst[2];
-    uint32_t bytes[2];
-    __device__ RowCopy() : src{nullptr, nullptr}, dst{nullptr, nullptr}, bytes{0u, 0u} {}
-    __device__ RowCopy(unsigned char* dst0, const unsigned char* plane, int ystart, int rows, int ny, uint32_t row_bytes) {
-        int y = ystart;
-        if (y < 0) y += ny;
-        else if (y >= ny) y -= ny;
-        const int first = rows < ny - y ? rows : ny - y;
-        src[0] = plane + (size_t)y * row_bytes;
-        dst[0] = dst0;
-        bytes[0] = (uint32_t)first * row_bytes;
-        src[1] = plane;
-        dst[1] = dst0 + (size_t)first * row_bytes;
-        bytes[1] = (uint32_t)(rows - first) * row_bytes;
-    }
-    __device__ bool aligned() const {
-        return ((reinterpret_cast<uintptr_t>(src[0]) | reinterpret_cast<uintptr_t>(src[1]) |
-                 reinterpret_cast<uintptr_t>(dst[0]) | reinterpret_cast<uintptr_t>(dst[1]) | bytes[0] | bytes[1]) &
-                15) == 0;
-    }
-    __device__ uint32_t total() const { return bytes[0] + bytes[1]; }
-    __device__ void issue(uint64_t* bar, uint64_t pol) const {
-        if (bytes[0]) bulk_load(dst[0], src[0], bytes[0], bar, pol);
-        if (bytes[1]) bulk_load(dst[1], src[1], bytes[1], bar, pol);
-    }
-};
-
-// Issue one item's copies, one RowCopy per active lane: check every address, post the byte count
-// on `bar`, then copy. False (nothing issued, the pass aborted) when an address or size is not a
-// multiple of 16 bytes.
-__device__ inline bool stage_item(const FusedArgs& F, const RowCopy& rc, bool active, uint64_t* bar) {
-    const int lane = threadIdx.x & 31;
-    const bool ok = __all_sync(0xffffffffu, !active || rc.aligned());
-    if (!ok) {
-        if (lane == 0) atomicExch(F.abort, 1);
-        return false;
-    }
-    uint32_t bytes = active ? rc.total() : 0u;
-    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-    if (lane == 0) mbar_expect_tx(bar, bytes);
-    __syncwarp();
-    if (active) rc.issue(bar, l2_evict_first());
-    return true;
-}
-
-// The persistent loop of the staged pass (threads as fused_loop: kBlock compute threads and one
-// scheduler warp). `describe(it, d)` fills an item's slot pointers (lane 0); `copies(d, stage,
-// lane, rc)` gives lane `lane`'s RowCopy of a tile (false: none); `work(d, stage)` runs an item on
-// the compute threads; `retire(d, lane)` invalidates a B tile's inputs (see fused_retires).
-template <class Describe, class Copies, class Work, class Retire>
-__device__ inline void fused_staged_loop(const FusedArgs& F, int nx, int nxy, int nz, unsigned char* stages,
-                                         int stage_bytes, Describe&& describe, Copies&& copies, Work&& work,
-                                         Retire&& retire) {
-    __shared__ __align__(8) uint64_t full[2], empty[2];
-    __shared__ StagedItem desc[2];
-    const int per_phase = F.tiles + 1;
-    const int total = 2 * nz * per_phase;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kBlock / 32);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < kBlock) {  // compute warps: take the stages in turn
-        for (int k = 0;; ++k) {
-            const int s = k & 1;
-            const unsigned par = (k >> 1) & 1;
-            if (!mbar_try(&full[s], par)) {  // bounded: twice the scheduler's own limit
-                const long long t0 = global_ns();
-                while (!mbar_try(&full[s], par)) {
-                    if (load_acquire(F.abort)) return;
-                    if (global_ns() - t0 > 2 * F.timeout_ns) {
-                        atomicExch(F.abort, 1);
-                        return;
-                    }
-                }
-            }
-            const StagedItem d = desc[s];
-            if (d.item < 0) return;
-            work(d, stages + (size_t)s * stage_bytes);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
-        }
-    }
-    // scheduler warp
-    int k = 0;          // items handed to the compute warps
-    int published = 0;  // items of this block published, in order
-    auto finished = [&](int q) { return __all_sync(0xffffffffu, mbar_test(&empty[q & 1], (q >> 1) & 1)); };
-    auto publish_next = [&]() {
-        const StagedItem& d = desc[published & 1];
-        const FusedItem it{d.type, d.plane, d.j};
-        if (fused_retires(F, it)) retire(d, lane);
-        __syncwarp();  // every lane's invalidations precede lane 0's fence and flag
-        if (lane == 0) fused_publish(F, nz, it);
-        __syncwarp();
-        ++published;
-    };
-    // bounded wait for `cond`, publishing the block's finished items meanwhile; false on abort
-    auto wait_for = [&](auto&& cond) {
-        const long long t0 = global_ns();
-        unsigned ns = 32;
-        for (;;) {
-            while (published < k && finished(published)) publish_next();
-            if (cond()) return true;
-            int stop = 0;
-            if (lane == 0) {
-                stop = load_acquire(F.abort);
-                if (!stop && global_ns() - t0 > F.timeout_ns) {
-                    atomicExch(F.abort, 1);
-                    stop = 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, stop, 0)) return false;
-            __nanosleep(ns);
-            if (ns < 512) ns *= 2;
-        }
-    };
-    // the compute warps' next stage gets the end marker; after an abort they wait for the copies
-    // already issued to that stage before they read it
-    auto end_marker = [&](int s) {
-        if (lane == 0) {
-            desc[s].item = -1;
-            mbar_arrive(&full[s]);
-        }
-        __syncwarp();
-    };
-    const FusedItem none{-1, -1, -1};
-    int item = 0, ticket = 0;
-    if (lane == 0) {
-        item = atomicAdd(F.next, 1);
-        ticket = atomicAdd(F.next, 1);
-    }
-    item = __shfl_sync(0xffffffffu, item, 0);
-    for (;;) {
-        const int s = k & 1;
-        if (k >= 2 && !wait_for([&] { return published >= k - 1; })) return;  // stage s is free
-        if (item >= total) {
-            end_marker(s);
-            break;
-        }
-        const FusedItem it = fused_item(item, per_phase, nz, F.L);
-        if (lane == 0) {
-            StagedItem& d = desc[s];
-            d.item = item;
-            d.type = it.type;
-            d.plane = it.plane;
-            d.j = it.j;
-            describe(it, d);
-        }
-        __syncwarp();
-        unsigned char* stage = stages + (size_t)s * stage_bytes;
-        const bool tile = it.j < F.tiles;
-        if (tile && it.type == kPhaseA) {  // its inputs never change during the pass: copy at once
-            RowCopy rc;
-            const bool active = copies(desc[s], stage, lane, rc);
-            if (!stage_item(F, rc, active, &full[s])) {
-                end_marker(s);
-                return;
-            }
-        }
-        if (!fused_ready_warp(F, nz, it, none, nx, nxy, false) &&
-            !wait_for([&] { return fused_ready_warp(F, nz, it, none, nx, nxy, false); })) {
-            end_marker(s);
-            return;
-        }
-        if (tile && it.type == kPhaseB) {
-            RowCopy rc;
-            const bool active = copies(desc[s], stage, lane, rc);
-            if (!stage_item(F, rc, active, &full[s])) {
-                end_marker(s);
-                return;
-            }
-        }
-        if (lane == 0) mbar_arrive(&full[s]);
-        __syncwarp();
-        ++k;
-        while (published < k && finished(published)) publish_next();
-        item = __shfl_sync(0xffffffffu, ticket, 0);
-        if (lane == 0) ticket = atomicAdd(F.next, 1);
-    }
-    wait_for([&] { return published == k; });
-}
-
 // --- host-side launchers (one set per model) -----------------------------------------------
 // Each returns the number of kernels it enqueued (errors are read with cudaGetLastError).
 int mm_launch_step(const StepArgs& a, cudaStream_t st);
@@ -1125,11 +831,6 @@ int hv_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F,
 // Resident blocks per SM of the two-step kernel.
 int mm_fused2_occupancy(int storage, int media_mode);
 int hv_fused2_occupancy(int storage, int media_mode);
-// The staged pass (fused_staged_loop): stage_bytes per stage, two stages of dynamic shared memory.
-int mm_launch_fused2s(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, int stage_bytes, cudaStream_t st);
-int hv_launch_fused2s(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, int stage_bytes, cudaStream_t st);
-int mm_fused2s_occupancy(int storage, int media_mode, int stage_bytes);
-int hv_fused2s_occupancy(int storage, int media_mode, int stage_bytes);
 int hv_launch_record_step(const StepArgs& a, cudaStream_t st);
 int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
 int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st);

@@ -495,118 +495,6 @@ __global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA
     });
 }
 
-// The staged pass (fused_staged_loop): a tile cell pulls from the rows staged in shared memory,
-// direction d at stage[d][r][x - v_dx] (r: the cell's row within the tile, x wraps within the row);
-// phase A writes the intermediate slot, phase B the other A/B buffer, as in MMToRing / MMFromRing.
-template <int S, bool kToRing>
-struct MMStaged {
-    using T = typename Pack4<S>::T;
-    const T* stage;
-    int x, r, rows, nx;
-    T* out;    // phase A: the slot of the cell's plane
-    int base;  // phase A: the plane's first cell
-    int nxy;
-    template <int S2>
-    __device__ void pull(const StepArgs& a, const Neighbourhood&, float4 (&f)[12]) const {
-        static_for<0, 12>([&](auto dc) {
-            constexpr int d = decltype(dc)::value;
-            int xs = x - kMMV[d][0];
-            if constexpr (kMMV[d][0] > 0) {
-                if (xs < 0) xs += nx;
-            } else if constexpr (kMMV[d][0] < 0) {
-                if (xs >= nx) xs -= nx;
-            }
-            f[d] = Pack4<S>::unpack(stage[(d * rows + r) * nx + xs], a.inv_scale);
-        });
-    }
-    template <int S2>
-    __device__ void put(const StepArgs& a, int d, int i, float4 v) const {
-        if constexpr (kToRing) {
-            __stcg(out + (size_t)d * nxy + (i - base), Pack4<S>::pack(v, a.scale));
-        } else {
-            T* __restrict__ fout = static_cast<T*>(a.fout);
-            __stcs(fout + (size_t)d * a.g.n + i, Pack4<S>::pack(v, a.scale));
-        }
-    }
-};
-
-template <int S, int M>
-__global__ void __launch_bounds__(kFusedThreads, 2) mm_fused2s_kernel(StepArgs aA, StepArgs aB, FusedArgs F,
-                                                                       int stage_bytes) {
-    using T = typename Pack4<S>::T;
-    extern __shared__ __align__(128) unsigned char stages[];
-    const int nx = aA.g.nx, ny = aA.g.ny, nz = aA.g.nz, nxy = nx * ny;
-    const int rows = F.tile_cells / nx;  // rows per tile
-    auto slot = [&](int p) -> T* {
-        if (p == 0) return static_cast<T*>(F.lo);
-        if (p == nz - 1) return static_cast<T*>(F.hi);
-        return static_cast<T*>(F.ring) + (size_t)(p % F.R) * 12 * nxy;
-    };
-    auto describe = [&](const FusedItem& it, StagedItem& d) {
-        d.out[0] = slot(it.plane);
-        d.in[0][0] = slot((it.plane + nz - 1) % nz);
-        d.in[0][1] = slot(it.plane);
-        d.in[0][2] = slot((it.plane + 1) % nz);
-    };
-    // lane k < 12 copies direction k's rows y0 - v_ky .. of plane p - v_kz: from the A/B buffer in
-    // phase A, from the intermediate slot in phase B
-    auto copies = [&](const StagedItem& d, unsigned char* stage, int lane, RowCopy& rc) {
-        if (lane >= 12) return false;
-        const int y0 = d.j * rows, nrows = min(rows, ny - y0);
-        const uint32_t row_bytes = (uint32_t)(nx * sizeof(T));
-        static_for<0, 12>([&](auto dc) {
-            constexpr int k = decltype(dc)::value;
-            if (lane == k) {
-                constexpr int vy = kMMV[k][1], vz = kMMV[k][2];
-                const int q = (d.plane - vz + nz) % nz;
-                const T* plane = d.type == kPhaseA
-                                     ? static_cast<const T*>(aA.fin) + (size_t)k * aA.g.n + (size_t)q * nxy
-                                     : static_cast<const T*>(d.in[0][1 - vz]) + (size_t)k * nxy;
-                rc = RowCopy(stage + (size_t)k * rows * row_bytes, reinterpret_cast<const unsigned char*>(plane),
-                             y0 - vy, nrows, ny, row_bytes);
-            }
-        });
-        return true;
-    };
-    auto work = [&](const StagedItem& d, const unsigned char* stage) {
-        const int p = d.plane, base = p * nxy;
-        if (d.j < F.tiles) {
-            const T* st = reinterpret_cast<const T*>(stage);
-            const int y0 = d.j * rows, ncell = min(rows, ny - y0) * nx, first = base + y0 * nx;
-            for (int c = threadIdx.x; c < ncell; c += kBlock) {
-                const int r = rows == 1 ? 0 : (int)(((unsigned long long)(unsigned)c * aA.g.mx) >> (32 + aA.g.kx));
-                const int x = c - r * nx;
-                if (d.type == kPhaseA)
-                    mm_update<S, M, false, false, false>(
-                        aA, first + c, 0, MMStaged<S, true>{st, x, r, rows, nx, static_cast<T*>(d.out[0]), base, nxy});
-                else
-                    mm_update<S, M, false, false, false>(aB, first + c, 0,
-                                                         MMStaged<S, false>{st, x, r, rows, nx, nullptr, base, nxy});
-            }
-        } else if (d.type == kPhaseA) {
-            const MMToRing<S> io{static_cast<T*>(d.out[0]), base, nxy};
-            for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
-                mm_update<S, M, true, false, false>(aA, aA.sv.cell[m], m, io);
-        } else {
-            const MMFromRing<S> io{{static_cast<const T*>(d.in[0][0]), static_cast<const T*>(d.in[0][1]),
-                                    static_cast<const T*>(d.in[0][2])},
-                                   nxy};
-            for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
-                mm_update<S, M, true, false, false>(aB, aB.sv.cell[m], m, io);
-        }
-    };
-    // the intermediate rows a B tile pulled: direction k from rows y - v_ky of plane p - v_kz
-    auto retire = [&](const StagedItem& d, int lane) {
-        const int y0 = d.j * rows, nrows = min(rows, ny - y0);
-        static_for<0, 12>([&](auto dc) {
-            constexpr int k = decltype(dc)::value;
-            const T* dir = static_cast<const T*>(d.in[0][1 - kMMV[k][2]]) + (size_t)k * nxy;
-            retire_rows<kMMV[k][1]>(dir, y0, nrows, nx, ny, lane);
-        });
-    };
-    fused_staged_loop(F, nx, nxy, nz, stages, stage_bytes, describe, copies, work, retire);
-}
-
 // ---------------------------------------------------------------------------------------------
 // Adjoint of one MM step. With per-velocity adjoints (a0^, a1^, c0^, c1^) of the post-collision
 // values, the transpose of eq. CollisionMiller through eq. equilibriumsMiller is
@@ -908,39 +796,6 @@ int mm_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F,
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             mm_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
-        });
-    });
-    return 1;
-}
-
-template <int S, int M>
-void mm_fused2s_smem(int stage_bytes) {
-    static int set = 0;  // the largest dynamic shared memory allowed so far (per instantiation)
-    if (2 * stage_bytes > set) {
-        cudaFuncSetAttribute(mm_fused2s_kernel<S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage_bytes);
-        set = 2 * stage_bytes;
-    }
-}
-
-int mm_fused2s_occupancy(int storage, int media_mode, int stage_bytes) {
-    int blocks = 0;
-    with_storage(storage, [&](auto sc) {
-        with_media(media_mode, [&](auto mc) {
-            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
-            mm_fused2s_smem<S, M>(stage_bytes);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mm_fused2s_kernel<S, M>, kFusedThreads,
-                                                          2 * (size_t)stage_bytes);
-        });
-    });
-    return blocks;
-}
-
-int mm_launch_fused2s(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, int stage_bytes, cudaStream_t st) {
-    const int grid = fused_grid(mm_fused2s_occupancy(aA.storage, aA.media_mode, stage_bytes));
-    with_storage(aA.storage, [&](auto sc) {
-        with_media(aA.media_mode, [&](auto mc) {
-            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
-            mm_fused2s_kernel<S, M><<<grid, kFusedThreads, 2 * (size_t)stage_bytes, st>>>(aA, aB, F, stage_bytes);
         });
     });
     return 1;

@@ -96,8 +96,6 @@ def load_library(path: str | None = None):
         "lbm_adjoint_release": (I, [P]),
         "lbm_set_step_fusion": (I, [P, I, I]),
         "lbm_step_fusion_active": (I, [P]),
-        "lbm_set_pass_shape": (I, [P, I, I, I, I]),
-        "lbm_pass_staged": (I, [P]),
         "lbm_fused_schedule_check": (I, [I, I, I, I, I, I]),
         "lbm_halo_bytes": (I64, [P]),
         "lbm_halo_pack": (I, [P, I, P, I]),
@@ -302,19 +300,6 @@ class Lattice:
         planes fit in L2; 2: whenever the lattice allows it. tile_cells: cells per work item of a
         pass (multiple of 256; 0 keeps the current value) (lbm_set_step_fusion)."""
         self._check(self.lib.lbm_set_step_fusion(self.h, int(mode), int(tile_cells)))
-
-    def set_pass_shape(self, ring: int = 0, lookahead: int = 0, staged: int = -1, discard: int = 0) -> None:
-        """Ring slots, lookahead, shared-memory staging and L2 line discards of the two-step pass
-        (0 / -1: defaults) (lbm_set_pass_shape)."""
-        self._check(self.lib.lbm_set_pass_shape(self.h, int(ring), int(lookahead), int(staged), int(discard)))
-
-    @property
-    def pass_staged(self) -> bool:
-        """Whether a two-step pass stages its inputs in shared memory (lbm_pass_staged)."""
-        rc = int(self.lib.lbm_pass_staged(self.h))
-        if rc < 0:
-            self._check(rc)
-        return rc == 1
 
     @property
     def step_fusion_active(self) -> bool:

@@ -124,98 +124,3 @@ def test_fusion_mode_is_checked():
         with pytest.raises(LbmError):
             L.set_step_fusion(mode, tile)
     L.close()
-
-
-# --- the staged pass (lbm_set_pass_shape: item inputs copied to shared memory) -------------------
-
-def run_pass(w, f, steps, mode=2, staged=-1, discard=0, tile=0, ring=0, lookahead=0, **kw):
-    from paper_2309_08068_gb300.lbm import lattice_from_workload
-    L = lattice_from_workload(w, init=False, **kw)
-    L.set_step_fusion(mode, tile)
-    L.set_pass_shape(ring, lookahead, staged, discard)
-    flags = L.step_fusion_active, L.pass_staged
-    L.set_populations(np.asarray(f, np.float32), 0)
-    L.step(steps)
-    out = L.populations_host(), L.fields_host("EBJ"), L.time
-    L.close()
-    return flags, out
-
-
-# (nx, ny): one row per item; two rows (the rows a tile pulls wrap past row 0); four rows with a
-# short last item (611 = 4 * 152 + 3)
-STAGED_PLANES = [(256, 160), (128, 305), (64, 611)]
-
-
-@pytest.mark.parametrize("model", ["mm", "hv"])
-@pytest.mark.parametrize("media", ["random", "few", "vacuum"])
-@pytest.mark.parametrize("plane", STAGED_PLANES)
-def test_staged_pass_equals_single_steps(model, media, plane):
-    w, f = wl.slab_case(model, plane + (6,), seed=140 + plane[0], media=media)
-    q = 48 if model == "mm" else 36
-    (active, staged), fused = run_pass(w, f, 5, staged=1)
-    assert active and staged
-    _, single = run_pass(w, f, 5, mode=0)
-    assert_same(fused, single, q)
-
-
-@pytest.mark.parametrize("model", ["mm", "hv"])
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
-def test_staged_pass_equals_single_steps_in_16_bit_storage(model, storage):
-    w, f = wl.slab_case(model, (128, 305, 6), seed=150, amplitude=1e-3)
-    kw = dict(storage=storage, storage_scale=2.0 ** 12 if storage == "f16" else 0.0)
-    q = 48 if model == "mm" else 36
-    (active, staged), fused = run_pass(w, f, 6, staged=1, **kw)
-    assert active and staged
-    _, single = run_pass(w, f, 6, mode=0, **kw)
-    assert_same(fused, single, q)
-
-
-@pytest.mark.parametrize("model", ["mm", "hv"])
-@pytest.mark.parametrize("staged", [0, 1])
-def test_discarded_lines_do_not_change_results(model, staged):
-    """B tiles that invalidate the intermediate lines they read: the source-cell tiles keep theirs
-    (slab_case puts source cells in every plane), every other tile drops them."""
-    w, f = wl.slab_case(model, (256, 160, 9), seed=160)
-    q = 48 if model == "mm" else 36
-    (active, st), fused = run_pass(w, f, 6, staged=staged, discard=1)
-    assert active and st == bool(staged)
-    _, single = run_pass(w, f, 6, mode=0)
-    assert_same(fused, single, q)
-
-
-@pytest.mark.parametrize("model", ["mm", "hv"])
-@pytest.mark.parametrize("ring,lookahead", [(3, 2), (4, 3), (8, 6)])
-def test_staged_pass_for_other_ring_depths(model, ring, lookahead):
-    w, f = wl.slab_case(model, (256, 160, 13), seed=170)
-    q = 48 if model == "mm" else 36
-    (active, staged), fused = run_pass(w, f, 4, staged=1, ring=ring, lookahead=lookahead)
-    assert active and staged
-    _, single = run_pass(w, f, 4, mode=0)
-    assert_same(fused, single, q)
-
-
-def test_staging_applies_only_where_it_fits():
-    from paper_2309_08068_gb300.lbm import Lattice
-    def staged(shape, model="mm", tile=0, **kw):
-        L = Lattice(model, shape, **kw)
-        L.set_step_fusion(2, tile)
-        L.set_pass_shape(0, 0, 1, 0)
-        s = L.pass_staged
-        L.close()
-        return s
-    assert staged((256, 160, 8))
-    assert staged((256, 160, 8), model="hv")
-    assert not staged((512, 96, 8))                   # one MM row is 96 KB in FP32
-    assert staged((512, 96, 8), storage="f16", storage_scale=2.0 ** 12)  # 48 KB
-    assert not staged((300, 140, 8), tile=512)        # items are not whole rows
-    assert not staged((250, 160, 8), model="hv", storage="bf16")  # 250 x 4 B rows: not 16-byte multiples
-
-
-def test_pass_shape_is_checked():
-    from paper_2309_08068_gb300.lbm import Lattice, LbmError
-    L = Lattice("mm", (8, 8, 8))
-    for args in ((2, 2, 1, 0), (0, 1, 1, 0), (65, 0, 1, 0), (-1, 0, 1, 0), (0, 0, 2, 0), (0, 0, 1, 2)):
-        with pytest.raises(LbmError):
-            L.set_pass_shape(*args)
-    L.set_pass_shape(7, 5, 0, 1)
-    L.close()
