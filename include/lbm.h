@@ -214,8 +214,9 @@ int lbm_destroy(lbm_ctx* ctx);
  * each pair of steps reads and writes the populations in HBM once instead of twice. The results
  * equal single steps bit for bit (same arithmetic; the intermediate planes hold the populations in
  * the context's storage format).
- *   mode 0: never; 1 (default): when the intermediate planes (R + 2 planes of populations: R = 5
- *   for MM, 6 for HV) fit in three quarters of L2 and a plane has at least 256 cells per SM;
+ *   mode 0: never; 1 (default): with FP32 storage, when the intermediate planes (R + 2 planes of
+ *   populations: R = 5 for MM, 6 for HV) fit in three quarters of L2 and a plane has at least 256
+ *   cells per SM (with 16-bit storage the single-step kernels are faster on GB300);
  *   2: whenever a plane has that many cells.
  * Never for z_ghost slabs or track_rho contexts, nor with nz < 4 (MM) or 5 (HV). The pass's dependency waits are
  * bounded (2 s); if one expires the pass stops, and the next lbm_sync, lbm_reduce or host-side

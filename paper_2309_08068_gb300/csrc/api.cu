@@ -235,7 +235,8 @@ size_t fused_plane_bytes(const lbm_ctx* c) {
 }
 
 // Pairs of steps run as one pass when the wavefront has enough tiles per plane to fill the GPU and
-// (mode 1) the intermediate planes fit in three quarters of L2, where they are meant to stay.
+// (mode 1) the populations are stored in FP32 and the intermediate planes fit in three quarters
+// of L2, where they are meant to stay.
 bool fusion_eligible(const lbm_ctx* c) {
     if (c->fusion == 0 || c->z_ghost || c->track_rho || c->g.nz < std::max(3, fused_shape(c).L + 1)) return false;
     int dev = 0, sms = 0, l2 = 0;
@@ -247,6 +248,10 @@ bool fusion_eligible(const lbm_ctx* c) {
     }
     if (c->g.nx * c->g.ny < sms * kBlock) return false;
     if (c->fusion == 1 && (fused_shape(c).R + 2) * fused_plane_bytes(c) > (size_t)l2 / 4 * 3) return false;
+    // With 16-bit storage the single-step kernels move so few bytes that they beat the pass, whose
+    // time is set by its wavefront's latency, not by its bytes (256^3 dipole on GB300: MM 0.50 ms
+    // per step against 0.62, HV 0.36 against 0.49).
+    if (c->fusion == 1 && c->storage != LBM_F32) return false;
     return true;
 }
 

@@ -247,10 +247,24 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
         if (p == nz - 1) return static_cast<T2*>(F.hi2);
         return static_cast<T2*>(F.ring2) + (size_t)(p % F.R) * 6 * nxy;
     };
-    fused_loop(F, aA.g.nx, nxy, nz, [&](int type, int p, int j) {
-        const int base = p * nxy;
-        if (type == kPhaseA) {
-            const HVToRing<S> io{slot(p), slot2(p), base, nxy};
+    auto describe = [&](const FusedItem& it, FusedDesc& d) {
+        if (it.type == kPhaseA) {
+            d.ptr[0] = slot(it.plane);
+            d.ptr[1] = slot2(it.plane);
+        } else {
+            const int pm = (it.plane + nz - 1) % nz, pp = (it.plane + 1) % nz;
+            d.ptr[0] = slot(pm);
+            d.ptr[1] = slot(it.plane);
+            d.ptr[2] = slot(pp);
+            d.ptr[3] = slot2(pm);
+            d.ptr[4] = slot2(it.plane);
+            d.ptr[5] = slot2(pp);
+        }
+    };
+    fused_loop(F, aA.g.nx, nxy, nz, describe, [&](const FusedDesc& d) {
+        const int p = d.plane, j = d.j, base = p * nxy;
+        if (d.type == kPhaseA) {
+            const HVToRing<S> io{static_cast<T4*>(d.ptr[0]), static_cast<T2*>(d.ptr[1]), base, nxy};
             if (j < F.tiles) {
                 const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
                 for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
@@ -260,8 +274,11 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
                     hv_update<S, M, true, false>(aA, aA.sv.cell[m], m, io);
             }
         } else {
-            const int pm = (p + nz - 1) % nz, pp = (p + 1) % nz;
-            const HVFromRing<S> io{{slot(pm), slot(p), slot(pp)}, {slot2(pm), slot2(p), slot2(pp)}, nxy};
+            const HVFromRing<S> io{{static_cast<const T4*>(d.ptr[0]), static_cast<const T4*>(d.ptr[1]),
+                                    static_cast<const T4*>(d.ptr[2])},
+                                   {static_cast<const T2*>(d.ptr[3]), static_cast<const T2*>(d.ptr[4]),
+                                    static_cast<const T2*>(d.ptr[5])},
+                                   nxy};
             if (j < F.tiles) {
                 const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
                 for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)

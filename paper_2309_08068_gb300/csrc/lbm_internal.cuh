@@ -714,10 +714,19 @@ __device__ __forceinline__ void named_arrive(int id, int count) {
 // always proceed (every item waits only for earlier ones); and in the usual case neither the
 // check nor the publication's fence delays the compute threads. Item n+1's dependence on n
 // itself is not looked up: the block's barriers order n before n+1.
-template <class Work>
-__device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, Work&& work) {
+// The scheduler also works out what the compute threads need of an item (`describe`: phase,
+// plane, tile and the ring slots it reads or writes) while they run the previous one, and hands
+// it over in shared memory, so the compute threads do no index arithmetic per item.
+struct FusedDesc {
+    int type, plane, j;
+    void* ptr[6];
+};
+
+template <class Describe, class Work>
+__device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, Describe&& describe, Work&& work) {
     constexpr int kHandoff = 1, kDone = 2;
     __shared__ int s_item[2], s_ok[2];
+    __shared__ FusedDesc s_desc[2];
     const int per_phase = F.tiles + 1;
     const int total = 2 * nz * per_phase;
     if (threadIdx.x < kBlock) {
@@ -725,14 +734,21 @@ __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, W
             named_sync(kHandoff, kFusedThreads);
             const int item = s_item[buf];
             if (item >= total || !s_ok[buf]) return;
-            const FusedItem it = fused_item(item, per_phase, nz, F.L);
-            work(it.type, it.plane, it.j);
+            work(s_desc[buf]);
             named_arrive(kDone, kFusedThreads);
         }
     }
     // scheduler warp
     const int lane = threadIdx.x & 31;
     const FusedItem none{-1, -1, -1};
+    auto make_desc = [&](const FusedItem& it) {
+        FusedDesc d;
+        d.type = it.type;
+        d.plane = it.plane;
+        d.j = it.j;
+        describe(it, d);
+        return d;
+    };
     int item = 0;
     if (lane == 0) item = atomicAdd(F.next, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
@@ -740,6 +756,7 @@ __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, W
     if (lane == 0) {
         s_item[0] = item;
         s_ok[0] = ok ? 1 : 0;
+        if (item < total) s_desc[0] = make_desc(fused_item(item, per_phase, nz, F.L));
     }
     named_arrive(kHandoff, kFusedThreads);
     for (int buf = 1;; buf ^= 1) {
@@ -750,12 +767,15 @@ __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, W
         nxt = __shfl_sync(0xffffffffu, nxt, 0);
         const FusedItem next = nxt < total ? fused_item(nxt, per_phase, nz, F.L) : none;
         const bool ready = nxt >= total || fused_ready_warp(F, nz, next, cur, nx, nxy, false);
+        FusedDesc nd;
+        if (lane == 0 && nxt < total) nd = make_desc(next);
         named_sync(kDone, kFusedThreads);  // the compute threads finished `cur`
         bool ok2 = true;
         if (ready) {
             if (lane == 0) {
                 s_item[buf] = nxt;
                 s_ok[buf] = 1;
+                if (nxt < total) s_desc[buf] = nd;
             }
             named_arrive(kHandoff, kFusedThreads);
             if (lane == 0) fused_publish(F, nz, cur);
@@ -766,6 +786,7 @@ __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, W
             if (lane == 0) {
                 s_item[buf] = nxt;
                 s_ok[buf] = ok2 ? 1 : 0;
+                if (nxt < total) s_desc[buf] = nd;
             }
             named_arrive(kHandoff, kFusedThreads);
         }

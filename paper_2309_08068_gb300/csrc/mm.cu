@@ -469,10 +469,19 @@ __global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA
         if (p == nz - 1) return static_cast<T*>(F.hi);
         return static_cast<T*>(F.ring) + (size_t)(p % F.R) * 12 * nxy;
     };
-    fused_loop(F, aA.g.nx, nxy, nz, [&](int type, int p, int j) {
-        const int base = p * nxy;
-        if (type == kPhaseA) {
-            const MMToRing<S> io{slot(p), base, nxy};
+    auto describe = [&](const FusedItem& it, FusedDesc& d) {
+        if (it.type == kPhaseA) {
+            d.ptr[0] = slot(it.plane);
+        } else {
+            d.ptr[0] = slot((it.plane + nz - 1) % nz);
+            d.ptr[1] = slot(it.plane);
+            d.ptr[2] = slot((it.plane + 1) % nz);
+        }
+    };
+    fused_loop(F, aA.g.nx, nxy, nz, describe, [&](const FusedDesc& d) {
+        const int p = d.plane, j = d.j, base = p * nxy;
+        if (d.type == kPhaseA) {
+            const MMToRing<S> io{static_cast<T*>(d.ptr[0]), base, nxy};
             if (j < F.tiles) {
                 const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
                 for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
@@ -482,7 +491,9 @@ __global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA
                     mm_update<S, M, true, false, false>(aA, aA.sv.cell[m], m, io);
             }
         } else {
-            const MMFromRing<S> io{{slot((p + nz - 1) % nz), slot(p), slot((p + 1) % nz)}, nxy};
+            const MMFromRing<S> io{{static_cast<const T*>(d.ptr[0]), static_cast<const T*>(d.ptr[1]),
+                                    static_cast<const T*>(d.ptr[2])},
+                                   nxy};
             if (j < F.tiles) {
                 const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
                 for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)

@@ -106,6 +106,8 @@ def test_fusion_switches_on_only_where_allowed():
     assert active(PLANE + (4,), mode=2)
     assert not active((512, 512, 6))                      # 7 x 50 MB does not fit in L2
     assert active((512, 512, 6), mode=2)
+    assert not active(PLANE + (11,), storage="f16", storage_scale=2.0 ** 12)  # single steps are faster
+    assert active(PLANE + (11,), mode=2, storage="bf16")
 
 
 def test_hv_needs_five_planes():
