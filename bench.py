@@ -562,6 +562,8 @@ def run_ours(args):
     single_gbs = {m: bpc1[m] * ncell / (single[m] * 1e-3) / 1e9 for m in single}
     cores = cpu_cores()
     cpu_mlups, cpu_steps, cpu_s = oracle_mlups(64, args.cpu_seconds, cores)
+    # the same oracle on one thread, on a smaller sample (a fifth of the all-core budget)
+    st_mlups, st_steps, st_s = oracle_mlups(32, args.cpu_seconds / 5, 1)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
@@ -596,7 +598,9 @@ def run_ours(args):
                      "frac": round(mm_gbs / peak, 4),
                      "traffic": None if traffic is None else round(traffic)},
         "cpu_baseline": {"value": round(cpu_mlups, 4), "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": f"64^3 dipole lattice per model, FP64, {cpu_steps} steps, {cpu_s:.1f} s"},
+                         "sample": f"64^3 dipole lattice per model, FP64, {cpu_steps} steps, {cpu_s:.1f} s",
+                         "single_thread": {"value": round(st_mlups, 4), "cores": 1,
+                                           "sample": f"32^3 dipole lattice per model, {st_steps} steps, {st_s:.1f} s"}},
         "e2e": {"value": round(job_value(2 * ncell, e2e_steps, world, e2e_s), 2), "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
                 "job": f"lbm_init_fields from pinned host E, B + {e2e_steps} steps + lbm_fields E, B to host"},
