@@ -19,7 +19,7 @@
  *     (vi)  imposed cells: f' := f_eq(E_imp(t), B_imp(t), J = 0)           (Appendix B "impose fields")
  *     (vii) advection f(x + v, t + 1) = f'(x, t), periodic on every axis
  *
- * Readings where the paper is silent (each is listed with its reason in the design notes):
+ * Readings taken where the paper is silent or ambiguous:
  *   - MM units eps0 = 1, mu0 = 2 (Section II-A); H reported as B / (mu0 mu_r).
  *   - MM with both an ohmic sigma and an external current: E = (D'/eps_r - mu0 J_ext/(4 eps_r)) /
  *     (1 + mu0 sigma/(4 eps_r)), J = sigma E + J_ext; it reduces to each printed form.

@@ -5,7 +5,7 @@ CPU). FP32 storage must reproduce the oracle's error at every resolution, which 
 convergence order. 16-bit storage does not preserve it. Each step rounds every population to 8 (BF16)
 or 11 (FP16) bits, and that noise grows like the square root of the step count, which itself grows
 with Lz. So storage error overtakes discretisation error after the first refinement (FP16) or
-immediately (BF16). The test records those errors (printed for the design notes) and checks only what
+immediately (BF16). The test prints those errors and checks only what
 holds: no storage beats the FP64 discretisation error, and FP16 still tracks it on the coarsest grid.
 """
 import numpy as np

@@ -152,7 +152,7 @@ def test_slab_pulse_full_size_against_its_1d_reduction(model):
     w1 = rounded(wl.slab_pulse(model, shape=(512, 1, 1)))
     G = lattice_from_workload(w3)
     O = oracle_from_workload(w1, threads=4)
-    steps = 3000 if model == "mm" else 1000  # HV grows exponentially in this medium (see the design notes)
+    steps = 3000 if model == "mm" else 1000  # HV grows exponentially in this medium, even in FP64
     G.step(steps)
     O.step(steps)
     F = G.fields("EB")

@@ -5,8 +5,8 @@ Tolerance derived from the arithmetic. Each step rounds every stored population 
 precision: unit roundoff u = 2^-8 for BF16 and 2^-11 for FP16. The rounding errors are independent
 and the step does not amplify them. After T steps, plus the rounding of the initial state, the
 relative L2 error is therefore about u * sqrt((T + 1) / 3). The element-wise tests allow 3 * u *
-sqrt(T + 1). The long 1500-step pulse records its error and guards it with a loose bound; the
-figures are stated in the design notes.
+sqrt(T + 1). The long 1500-step pulse records its error and guards it with a loose bound (measured
+on GB300: 2-3 % for FP16, 10-21 % for BF16).
 """
 import numpy as np
 import pytest
