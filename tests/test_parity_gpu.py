@@ -208,6 +208,60 @@ def test_full_size_dipole_step_sampled(model):
     assert max(errs) <= TOL, max(errs)
 
 
+@pytest.mark.parametrize("model", MODELS)
+def test_large_lattice_two_step_pass_sampled(model):
+    """384^3 lattice (56.6 M cells) whose planes are too large for the pass's ring to stay in L2
+    (forced on with mode 2): random populations, one two-step pass, then each sampled cell is
+    recomputed by the oracle from its own 5 x 5 x 5 neighbourhood. Two steps reach two cells, so
+    that block determines the centre exactly. Samples include the wrap-around planes 0 and nz - 1
+    and the dipole source."""
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    n = 384
+    w = rounded(wl.hertz_dipole(model, n=n))
+    q = 48 if model == "mm" else 36
+    G = lattice_from_workload(w, init=False)
+    G.set_step_fusion(2)
+    assert G.step_fusion_active
+    gen = torch.Generator(device="cuda").manual_seed(22)
+    f0 = torch.randn((wl.POPULATIONS[model], n ** 3), generator=gen, device="cuda", dtype=torch.float32)
+    if model == "mm":
+        f0[48:] = 0.0  # rest populations are not stored without track_rho
+    t0 = 11
+    G.set_populations(f0, t0)
+    before = G.launch_count
+    G.step(2)
+    launches = G.launch_count - before
+    f2 = G.populations()
+    rng = np.random.default_rng(6)
+    c = n // 2
+    samples = [(0, 0, 0), (n - 1, n - 1, n - 1), (5, n - 1, 0), (n - 1, 3, n - 1), (c, c, c), (c + 2, c - 1, c + 3)]
+    samples += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(24)]
+    samples += [tuple(int(v) for v in c + rng.integers(-7, 8, 3)) for _ in range(24)]
+    src = w.sources[0]
+    src_w = {int(cell): src.w[k] for k, cell in enumerate(src.cells)}
+    from oracle import OracleLattice, TimeFn
+    errs = []
+    for (x, y, z) in samples:
+        xs = [(x + d) % n for d in range(-2, 3)]
+        ys = [(y + d) % n for d in range(-2, 3)]
+        zs = [(z + d) % n for d in range(-2, 3)]
+        cells = np.array([xx + n * (yy + n * zz) for zz in zs for yy in ys for xx in xs], dtype=np.int64)
+        block = f0[:, torch.from_numpy(cells).cuda()].cpu().numpy().astype(np.float64)
+        O = OracleLattice(model, (5, 5, 5))
+        local = [(k, src_w[int(cell)]) for k, cell in enumerate(cells) if int(cell) in src_w]
+        if local:
+            O.add_current([k for k, _ in local], np.array([v for _, v in local]),
+                          TimeFn("sin", src.fn.amplitude, src.fn.period, src.fn.phase))
+        O.set_populations(block, t0)
+        O.step(2)
+        ref = O.populations()[:q, 62]
+        got = f2[:q, x + n * (y + n * z)].cpu().numpy()
+        errs.append(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-30))
+    G.close()
+    assert launches == 1  # the two steps ran as one pass
+    assert max(errs) <= TOL, max(errs)
+
+
 # ---------------------------------------------------------------------------------------------
 # API behaviour on the GPU
 # ---------------------------------------------------------------------------------------------
