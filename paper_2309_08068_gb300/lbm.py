@@ -142,6 +142,10 @@ class Lattice:
 
     ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream). Media are per-cell
     arrays (numpy or torch CUDA), None for eps_r = mu_r = 1, sigma = 0.
+
+    Device tensors passed in or returned are ordered against torch's current stream: the library's
+    stream waits for what the current stream has queued before it reads or writes them, and the
+    current stream waits for the library's work before the tensors are used there.
     """
 
     def __init__(self, model: str, shape, eps_r=None, mu_r=None, sigma=None, *, track_rho: bool = False,
@@ -176,12 +180,35 @@ class Lattice:
         self.storage = storage
         self.z_ghost = bool(z_ghost)
         h = ctypes.c_void_p()
+        if media.on_device:
+            self._inputs_ready()
         rc = self.lib.lbm_create(MODELS[model], nx, ny, nz, ctypes.byref(media), ctypes.byref(opts), ctypes.byref(h))
         if rc != 0:
             raise LbmError(rc, self.lib.lbm_last_error(None).decode())
         self.h = h
+        if media.on_device:
+            self._outputs_ready(*keep)
 
     # -- plumbing --------------------------------------------------------------------------
+    def _inputs_ready(self):
+        """The context stream waits for the work torch's current stream has queued (device inputs
+        written there, output tensors allocated there)."""
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _outputs_ready(self, *tensors):
+        """torch's current stream waits for the context stream, and each torch tensor's memory stays
+        reserved until the context stream has finished with it."""
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+            for t in tensors:
+                if isinstance(t, torch.Tensor) and t.is_cuda:
+                    t.record_stream(self.stream)
+
     def _check(self, rc: int):
         if rc != 0:
             raise LbmError(rc, self.lib.lbm_last_error(self.h).decode())
@@ -215,7 +242,11 @@ class Lattice:
         pb, db, kb = _as_f32(B, 3 * self.n, "B")
         if de != db:
             raise ValueError("E and B must both be host or both be device arrays")
+        if de:
+            self._inputs_ready()
         self._check(self.lib.lbm_init_fields(self.h, pe, pb, de))
+        if de:
+            self._outputs_ready(ke, kb)
 
     def add_source(self, src):
         """``src``: a ``workloads.Source``."""
@@ -248,7 +279,9 @@ class Lattice:
         mask = sum(FIELD_BITS[c] for c in names)
         if out is None:
             out = torch.empty((len(names), 3, self.n), dtype=torch.float32, device=self.device)
+        self._inputs_ready()
         self._check(self.lib.lbm_fields(self.h, mask, out.data_ptr(), 1))
+        self._outputs_ready(out)
         return {c: out[k] for k, c in enumerate(names)}
 
     def fields_host(self, names: str = "EB") -> dict:
@@ -263,7 +296,9 @@ class Lattice:
         """Populations in the canonical layout, torch CUDA tensor (q, n)."""
         import torch
         out = torch.empty((self.q, self.n), dtype=torch.float32, device=self.device)
+        self._inputs_ready()
         self._check(self.lib.lbm_get_populations(self.h, out.data_ptr(), 1))
+        self._outputs_ready(out)
         return out
 
     def populations_host(self) -> np.ndarray:
@@ -273,7 +308,11 @@ class Lattice:
 
     def set_populations(self, f, t: int = 0):
         p, dev, k = _as_f32(f, self.q * self.n, "populations")
+        if dev:
+            self._inputs_ready()
         self._check(self.lib.lbm_set_populations(self.h, p, dev, int(t)))
+        if dev:
+            self._outputs_ready(k)
 
     def reduce(self):
         """(field energy, sum of squared populations, MM total charge), double precision."""
@@ -290,8 +329,10 @@ class Lattice:
         ge = torch.empty(self.n, dtype=torch.float32, device=self.device)
         gs = torch.empty(self.n, dtype=torch.float32, device=self.device)
         loss = ctypes.c_double()
+        self._inputs_ready()
         self._check(self.lib.lbm_adjoint(self.h, int(steps), int(plane_axis), int(plane_index), int(checkpoint_interval),
                                          ctypes.byref(loss), ge.data_ptr(), gs.data_ptr(), 1))
+        self._outputs_ready(ge, gs)
         return loss.value, ge, gs
 
     # -- two steps per pass ----------------------------------------------------------------------
@@ -321,14 +362,18 @@ class Lattice:
         import torch
         if out is None:
             out = torch.empty(self.halo_bytes, dtype=torch.uint8, device=self.device)
+        self._inputs_ready()
         self._check(self.lib.lbm_halo_pack(self.h, int(face), out.data_ptr(), 1))
+        self._outputs_ready(out)
         return out
 
     def halo_unpack(self, face: int, data) -> None:
         """Write a neighbour's packed face into ghost plane 0 (face 0) or nz - 1 (face 1)."""
         if data.numel() * data.element_size() != self.halo_bytes or not data.is_cuda:
             raise ValueError("halo_unpack: need a CUDA buffer of halo_bytes bytes")
+        self._inputs_ready()
         self._check(self.lib.lbm_halo_unpack(self.h, int(face), data.data_ptr(), 1))
+        self._outputs_ready(data)
 
     def halo_exchange(self, upper: "Lattice") -> None:
         """Exchange across the interface between this slab (below) and `upper` (lbm_halo_exchange)."""

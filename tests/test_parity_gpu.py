@@ -267,6 +267,33 @@ def test_large_lattice_two_step_pass_sampled(model):
 # ---------------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("model", MODELS)
+def test_device_tensors_are_ordered_against_the_current_stream(model):
+    """A lattice on a stream of its own, fed and read through torch's current stream: an input
+    produced late on the current stream (after a spin kernel) must be waited for, and outputs must
+    be complete before the current stream uses them."""
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    n = 96
+    w = rounded(wl.hertz_dipole(model, n=n))
+    stream = torch.cuda.Stream()
+    L = lattice_from_workload(w, stream=stream, init=False)
+    q = wl.POPULATIONS[model]
+    for rep in range(2):
+        torch.cuda._sleep(20_000_000)  # keeps the current stream busy for milliseconds
+        f = torch.randn((q, n ** 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(rep))
+        if model == "mm":
+            f[48:] = 0.0
+        L.set_populations(f, 3)
+        assert np.array_equal(L.populations_host(), f.cpu().numpy())
+        L.step(40)  # long enough that an unordered read would find the outputs unfinished
+        F = L.fields("EB")
+        P = L.populations()
+        got_e, got_p = F["E"].cpu().numpy(), P.cpu().numpy()
+        assert np.array_equal(got_e, L.fields_host("E")["E"])
+        assert np.array_equal(got_p, L.populations_host())
+    L.close()
+
+
+@pytest.mark.parametrize("model", MODELS)
 def test_checkpoint_resume_is_bitwise(model):
     w = wl.hertz_dipole(model, n=24, period=12.0)
     from paper_2309_08068_gb300.lbm import lattice_from_workload
