@@ -59,6 +59,19 @@ def test_fused_pairs_equal_single_steps_for_every_item_size(model, tile):
 
 
 @pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("plane", [(300, 140), (97, 409)])
+def test_fused_pairs_equal_single_steps_when_items_split_rows(model, plane):
+    """Planes whose rows are not a whole number of items: 256- and 512-cell items start mid-row, so a
+    tile's neighbourhood window covers partial rows and wraps around the plane."""
+    w, f = wl.slab_case(model, plane + (7,), seed=125)
+    q = 48 if model == "mm" else 36
+    active, fused = run(w, f, 5, 2)
+    assert active
+    _, single = run(w, f, 5, 0)
+    assert_same(fused, single, q)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_fused_pairs_equal_single_steps_in_16_bit_storage(model, storage):
     w, f = wl.slab_case(model, PLANE + (6,), seed=120, amplitude=1e-3)
