@@ -70,7 +70,7 @@ def compare_fields(G, O, names="EBDHJ", tol=TOL):
 # Random states: every population, every field, several tiles plus a ragged tail
 # ---------------------------------------------------------------------------------------------
 
-SHAPES = [(4, 4, 4), (5, 3, 2), (1, 1, 1), (1, 1, 16), (37, 19, 11)]
+SHAPES = [(4, 4, 4), (5, 3, 2), (1, 1, 1), (1, 1, 16), (16, 1, 1), (1, 16, 1), (7, 1, 5), (37, 19, 11)]
 
 
 @pytest.mark.parametrize("model", MODELS)
