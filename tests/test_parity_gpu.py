@@ -91,6 +91,28 @@ def test_random_state_parity(model, shape, media):
 
 
 @pytest.mark.parametrize("model", MODELS)
+def test_table_and_constant_time_functions(model):
+    """A current driven by a table, s(t) = amplitude table[t] and zero past the table's end, and an
+    imposed field driven by a constant, against the oracle. Iterations t = 3 .. 16 run; the
+    9-entry table covers t = 3 .. 8 of them."""
+    w, f = wl.random_state(model, (6, 5, 7), seed=31, media="few", n_sources=0)
+    rng = np.random.default_rng(32)
+    table = rng.standard_normal(9)
+    w.sources = [
+        wl.Source("current", np.array([3, 40, 100, 170]), wl.TimeFunction("table", 0.7, 1.0, 0.0, table),
+                  w=rng.standard_normal((4, 3))),
+        wl.Source("impose", np.array([11, 150]), wl.TimeFunction("const", 0.4), E0=tuple(rng.standard_normal(3)),
+                  B0=tuple(rng.standard_normal(3))),
+    ]
+    G, O = pair(w, f, t0=2, track_rho=model == "mm")
+    for steps in (4, 10):  # to t = 6 inside the table, then past its end
+        G.step(steps)
+        O.step(steps)
+        assert rel_l2(G.populations_host(), O.populations()) <= TOL
+        compare_fields(G, O)
+
+
+@pytest.mark.parametrize("model", MODELS)
 def test_rest_populations_and_charge(model):
     """MM keeps f_0^(0) (rho_c) and the inert f_0^(1) when asked; totals match the oracle."""
     w, f = wl.random_state(model, (6, 5, 4), seed=12, media="few", n_sources=1)
