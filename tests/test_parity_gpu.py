@@ -113,6 +113,35 @@ def test_table_and_constant_time_functions(model):
 
 
 @pytest.mark.parametrize("model", MODELS)
+def test_sixteen_overlapping_sources(model):
+    """The most sources a context takes (16): currents and imposed fields on cells that several of
+    them share (two currents, two imposed fields, and a current with an imposed field on one cell),
+    against the oracle. Currents on a cell add, imposed fields add. A 17th source is refused."""
+    from paper_2309_08068_gb300.lbm import LbmError
+    w, f = wl.random_state(model, (6, 5, 4), seed=33, media="random", n_sources=0)
+    rng = np.random.default_rng(34)
+    srcs = []
+    for k in range(16):
+        cells = np.unique(np.concatenate([rng.choice(w.n, size=5, replace=False), [7 if k % 2 else 9]]))
+        fn = wl.TimeFunction("sin", rng.uniform(0.5, 2.0), rng.uniform(5.0, 30.0), rng.uniform(0.0, 6.28))
+        if k % 3 == 2:
+            srcs.append(wl.Source("impose", cells, fn, E0=tuple(rng.standard_normal(3)),
+                                  B0=tuple(rng.standard_normal(3))))
+        else:
+            srcs.append(wl.Source("current", cells, fn, w=rng.standard_normal((cells.size, 3))))
+    w.sources = srcs
+    G, O = pair(w, f, t0=1, track_rho=model == "mm")
+    G.step(6)
+    O.step(6)
+    assert rel_l2(G.populations_host(), O.populations()) <= TOL
+    compare_fields(G, O)
+    extra = wl.Source("current", np.array([0]), wl.TimeFunction("const", 1.0), w=np.ones((1, 3)))
+    with pytest.raises(LbmError):
+        G.add_source(extra)
+    G.close()
+
+
+@pytest.mark.parametrize("model", MODELS)
 def test_rest_populations_and_charge(model):
     """MM keeps f_0^(0) (rho_c) and the inert f_0^(1) when asked; totals match the oracle."""
     w, f = wl.random_state(model, (6, 5, 4), seed=12, media="few", n_sources=1)
