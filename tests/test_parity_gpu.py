@@ -142,6 +142,24 @@ def test_sixteen_overlapping_sources(model):
 
 
 @pytest.mark.parametrize("model", MODELS)
+def test_field_masks_select_and_order_their_blocks(model):
+    """lbm_fields writes the selected fields in the order E, B, D, H, J, whatever the subset: every
+    subset's blocks equal the full selection's, bit for bit."""
+    import itertools
+    w, f = wl.random_state(model, (7, 6, 5), seed=35, media="random", n_sources=2)
+    G, _ = pair(w, f, t0=2)
+    G.step(3)
+    full = G.fields_host("EBDHJ")
+    for r in range(1, 6):
+        for names in itertools.combinations("EBDHJ", r):
+            sub = G.fields_host("".join(names))
+            assert list(sub) == list(names)
+            for c in names:
+                assert np.array_equal(sub[c], full[c]), (names, c)
+    G.close()
+
+
+@pytest.mark.parametrize("model", MODELS)
 def test_rest_populations_and_charge(model):
     """MM keeps f_0^(0) (rho_c) and the inert f_0^(1) when asked; totals match the oracle."""
     w, f = wl.random_state(model, (6, 5, 4), seed=12, media="few", n_sources=1)
