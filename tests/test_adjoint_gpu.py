@@ -172,3 +172,31 @@ def test_workspace_is_kept_grown_and_released(model):
     for r in (again, last):
         assert r[0] == first[0]
         assert np.array_equal(r[1], first[1]) and np.array_equal(r[2], first[2])
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_adjoint_refuses_what_it_does_not_support(model):
+    """16-bit storage, a source cell inside the loss plane, a plane index outside the lattice and a
+    z-slab context are refused with an error, and the context stays usable."""
+    from paper_2309_08068_gb300.lbm import Lattice, LbmError
+    shape = (6, 5, 4)
+    n = 6 * 5 * 4
+    L16 = Lattice(model, shape, storage="bf16")
+    with pytest.raises(LbmError):
+        L16.adjoint(3, 0, 2)
+    L16.close()
+    L = Lattice(model, shape)
+    src = wl.Source("current", np.array([2 + 6 * (1 + 5 * 1)]), wl.TimeFunction("const", 1.0), w=np.ones((1, 3)))
+    L.add_source(src)  # cell (2, 1, 1): in the plane x = 2
+    with pytest.raises(LbmError):
+        L.adjoint(3, 0, 2)
+    for axis, index in ((0, 6), (1, -1), (3, 0)):
+        with pytest.raises(LbmError):
+            L.adjoint(3, axis, index)
+    loss, ge, gs = L.adjoint(3, 0, 4)  # a plane without sources still works
+    assert np.isfinite(loss) and ge.shape == (n,) and bool(torch.isfinite(ge).all())
+    L.close()
+    S = Lattice(model, (6, 5, 5), z_ghost=True)
+    with pytest.raises(LbmError):
+        S.adjoint(3, 0, 2)
+    S.close()
