@@ -278,18 +278,19 @@ def test_full_size_dipole_step_sampled(model):
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_large_lattice_two_step_pass_sampled(model):
-    """384^3 lattice (56.6 M cells) whose planes are too large for the pass's ring to stay in L2
-    (forced on with mode 2): random populations, one two-step pass, then each sampled cell is
-    recomputed by the oracle from its own 5 x 5 x 5 neighbourhood. Two steps reach two cells, so
+@pytest.mark.parametrize("n,mode", [(256, 1), (384, 2)])
+def test_two_step_pass_sampled_at_full_size(model, n, mode):
+    """One two-step pass on the 256^3 dipole lattice in the benchmark's own configuration (mode 1,
+    default ring, lookahead and items), and on a 384^3 lattice (56.6 M cells) whose planes are too
+    large for the ring to stay in L2 (forced on with mode 2). Random populations; each sampled cell
+    is recomputed by the oracle from its own 5 x 5 x 5 neighbourhood. Two steps reach two cells, so
     that block determines the centre exactly. Samples include the wrap-around planes 0 and nz - 1
     and the dipole source."""
     from paper_2309_08068_gb300.lbm import lattice_from_workload
-    n = 384
     w = rounded(wl.hertz_dipole(model, n=n))
     q = 48 if model == "mm" else 36
     G = lattice_from_workload(w, init=False)
-    G.set_step_fusion(2)
+    G.set_step_fusion(mode)
     assert G.step_fusion_active
     gen = torch.Generator(device="cuda").manual_seed(22)
     f0 = torch.randn((wl.POPULATIONS[model], n ** 3), generator=gen, device="cuda", dtype=torch.float32)
