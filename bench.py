@@ -59,6 +59,44 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def l2_resident_bandwidth(stream, mb: int = 32, reps: int = 200):
+    """Copy and write rates on a buffer that stays in L2, timed outside the timed region with
+    torch's own copy and fill kernels, replayed from a CUDA graph (a 32 MB copy takes a few
+    microseconds, about what a launch from Python costs). This is the on-chip ceiling that the
+    two-step pass runs against, since its intermediate planes live in L2."""
+    import torch
+    n = mb * (1 << 20) // 4
+    with torch.cuda.stream(stream):
+        a = torch.ones(n, device="cuda")
+        b = torch.empty_like(a)
+        b.copy_(a)
+        b.fill_(2.0)
+    stream.synchronize()
+    graphs = {}
+    for name, op in (("copy", lambda: b.copy_(a)), ("write", lambda: b.fill_(2.0))):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(reps):
+                op()
+        graphs[name] = g
+    out = {"buffer_MB": mb, "kernels": "torch copy_ and fill_ in a CUDA graph"}
+    for name, g in graphs.items():
+        with torch.cuda.stream(stream):  # a graph replays on the current stream
+            g.replay()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                g.replay()
+            e1.record(stream)
+        e1.synchronize()
+        per_op_s = e0.elapsed_time(e1) * 1e-3 / (3 * reps)
+        moved = (2 if name == "copy" else 1) * n * 4  # a copy reads and writes the buffer
+        out[f"{name}_GBps"] = round(moved / per_op_s / 1e9, 1)
+    del graphs, a, b
+    return out
+
+
 def ncu_traffic(kernel: str, n_cells: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to n_cells, or None
     when the summary is missing or was taken on a different kernel source."""
@@ -560,6 +598,19 @@ def run_ours(args):
     traffic = ncu_traffic(kname["mm"], ncell) if args.storage == "f32" else None
     hv_traffic = ncu_traffic(kname["hv"], ncell) if args.storage == "f32" else None
     single_gbs = {m: bpc1[m] * ncell / (single[m] * 1e-3) / 1e9 for m in single}
+    l2 = l2_resident_bandwidth(stream)
+    # Second roofline, against L2 writes (stores from the SMs plus fills from HBM). Per cell, a
+    # single step writes its populations into L2 twice (the output, and the fill of its inputs from
+    # HBM); a two-step pass writes them three times per two steps (the ring slot, the output and
+    # the fill), 1.5 times per step. Every kernel here runs at about the L2-resident write rate.
+    pop = {m: bpc1[m] // 2 for m in bpc1}
+    l2w = {m: (3 * pop[m] // 2 if fused[m] else 2 * pop[m]) for m in pop}
+    step_ms = {"mm": mm_ms, "hv": hv_ms}
+    l2_roof = {m: {"kernel": kname[m], "bytes_per_cell_step": l2w[m],
+                   "achieved": round(l2w[m] * ncell / (step_ms[m] * 1e-3) / 1e9, 1), "peak": l2["write_GBps"],
+                   "unit": "GB/s"} for m in l2w}
+    for m in l2_roof:
+        l2_roof[m]["frac"] = round(l2_roof[m]["achieved"] / l2["write_GBps"], 4)
     cores = cpu_cores()
     cpu_mlups, cpu_steps, cpu_s = oracle_mlups(64, args.cpu_seconds, cores)
     # the same oracle on one thread, on a smaller sample (a fifth of the all-core budget)
@@ -597,6 +648,9 @@ def run_ours(args):
                      "achieved": round(mm_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(mm_gbs / peak, 4),
                      "traffic": None if traffic is None else round(traffic)},
+        "l2_resident": l2,
+        "l2_write_roofline": dict(l2_roof, note="L2 writes = stores from the SMs + fills from HBM; "
+                                  "peak = l2_resident.write_GBps"),
         "cpu_baseline": {"value": round(cpu_mlups, 4), "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
                          "sample": f"64^3 dipole lattice per model, FP64, {cpu_steps} steps, {cpu_s:.1f} s",
                          "single_thread": {"value": round(st_mlups, 4), "cores": 1,

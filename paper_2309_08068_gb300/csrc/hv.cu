@@ -117,7 +117,7 @@ __device__ __forceinline__ float3 hv_h(float3 B, const MatCoef& mat) {
 }
 
 // Where a step reads its populations and writes its results: the context's A/B buffers.
-struct HVBuffers {
+struct HVBuffers : NoStash {
     template <int S>
     __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) const {
         hv_pull<S>(a, h, e, hy);
@@ -135,6 +135,11 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m, const
     float4 e[6];
     float2 hy[6];
     io.template pull<S>(a, h, e, hy);
+    if constexpr (IO::kStash)  // the h pairs wait in shared memory until the collision
+        static_for<0, 6>([&](auto ic) {
+            constexpr int k = decltype(ic)::value;
+            io.stash_put(k, hy[k].x, hy[k].y);
+        });
     const MatCoef mat = load_coef<kModelHV, M>(a.media, i, a.eps0, a.mu0);
     CellSource cs;
     float3 jext = make_float3(0.f, 0.f, 0.f);
@@ -157,7 +162,9 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m, const
         if constexpr (A == 0) eo.x -= 0.5f * F.J.x;
         else if constexpr (A == 1) eo.y -= 0.5f * F.J.y;
         else eo.z -= 0.5f * F.J.z;
-        float3 ho = make_float3(p.x + vE.x - e[k].w, p.y + vE.y - hy[k].x, p.z + vE.z - hy[k].y);
+        float hyx = hy[k].x, hyy = hy[k].y;
+        if constexpr (IO::kStash) io.stash_get(k, hyx, hyy);
+        float3 ho = make_float3(p.x + vE.x - e[k].w, p.y + vE.y - hyx, p.z + vE.z - hyy);
         if constexpr (kSpecial) {
             if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
                 const float3 cH = axis_cross<A, G>(hv_h(cs.B, mat));
@@ -181,7 +188,7 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m, const
 // intermediate plane, phase B pulls from the intermediate planes (L2 loads) and streams the other
 // A/B buffers out. The arithmetic is hv_update's, so the results equal two single steps bit for bit.
 template <int S>
-struct HVToRing {
+struct HVToRing : FusedStash {
     using T4 = typename Pack4<S>::T;
     using T2 = typename Pack2<S>::T;
     T4* plane;
@@ -206,7 +213,7 @@ struct HVToRing {
 };
 
 template <int S>
-struct HVFromRing {
+struct HVFromRing : FusedStash {
     using T4 = typename Pack4<S>::T;
     using T2 = typename Pack2<S>::T;
     const T4* plane[3];  // slots of planes z - 1, z, z + 1
@@ -236,6 +243,8 @@ template <int S, int M>
 __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA, StepArgs aB, FusedArgs F) {
     using T4 = typename Pack4<S>::T;
     using T2 = typename Pack2<S>::T;
+    __shared__ float2 s_stash[6 * kBlock];  // the h pairs, [velocity][compute thread]
+    const unsigned stash = fused_stash_slot(s_stash);
     const int nz = aA.g.nz, nxy = aA.g.nx * aA.g.ny;
     auto slot = [&](int p) -> T4* {
         if (p == 0) return static_cast<T4*>(F.lo);
@@ -264,7 +273,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
     fused_loop(F, aA.g.nx, nxy, nz, describe, [&](const FusedDesc& d) {
         const int p = d.plane, j = d.j, base = p * nxy;
         if (d.type == kPhaseA) {
-            const HVToRing<S> io{static_cast<T4*>(d.ptr[0]), static_cast<T2*>(d.ptr[1]), base, nxy};
+            const HVToRing<S> io{{stash}, static_cast<T4*>(d.ptr[0]), static_cast<T2*>(d.ptr[1]), base, nxy};
             if (j < F.tiles) {
                 const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
                 for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
@@ -274,7 +283,8 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
                     hv_update<S, M, true, false>(aA, aA.sv.cell[m], m, io);
             }
         } else {
-            const HVFromRing<S> io{{static_cast<const T4*>(d.ptr[0]), static_cast<const T4*>(d.ptr[1]),
+            const HVFromRing<S> io{{stash},
+                                   {static_cast<const T4*>(d.ptr[0]), static_cast<const T4*>(d.ptr[1]),
                                     static_cast<const T4*>(d.ptr[2])},
                                    {static_cast<const T2*>(d.ptr[3]), static_cast<const T2*>(d.ptr[4]),
                                     static_cast<const T2*>(d.ptr[5])},

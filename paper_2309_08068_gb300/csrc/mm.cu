@@ -136,7 +136,7 @@ __device__ __forceinline__ void mm_put(const StepArgs& a, int d, int i, float4 v
 }
 
 // Where a step reads its populations and writes its results: the context's A/B buffers.
-struct MMBuffers {
+struct MMBuffers : NoStash {
     template <int S>
     __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) const {
         mm_pull<S>(a, h, f);
@@ -153,6 +153,11 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m, const
     const Neighbourhood h = neighbourhood(a.g, i);
     float4 f[12];
     io.template pull<S>(a, h, f);
+    if constexpr (IO::kStash)  // the f^(1) halves wait in shared memory until the collision
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            io.stash_put(d, f[d].z, f[d].w);
+        });
     const MatCoef mat = load_coef<kModelMM, M>(a.media, i, a.eps0, a.mu0);
     float rest0 = 0.f;
     if constexpr (kRho) rest0 = a.rho_in[i];
@@ -175,8 +180,10 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m, const
         float4 o;
         o.x = two_s + two_alpha - f[d].x;
         o.y = two_s - two_alpha - f[d].y;
-        o.z = two_s + two_beta - f[d].z;
-        o.w = two_s - two_beta - f[d].w;
+        float fz = f[d].z, fw = f[d].w;
+        if constexpr (IO::kStash) io.stash_get(d, fz, fw);
+        o.z = two_s + two_beta - fz;
+        o.w = two_s - two_beta - fw;
         if constexpr (kSpecial) {
             if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
                 const float bi = sdot<b0, b1, b2>(cs.B.x, cs.B.y, cs.B.z);
@@ -422,7 +429,7 @@ __global__ void __launch_bounds__(kBlock, 3) mm_record_kernel(StepArgs a) {
 // once (streaming stores). The arithmetic is mm_update's, so the pair of steps gives the same
 // bits as two single steps.
 template <int S>
-struct MMToRing {
+struct MMToRing : FusedStash {
     using T = typename Pack4<S>::T;
     T* plane;  // slot of this cell's plane
     int base;  // first cell of the plane
@@ -443,7 +450,7 @@ struct MMToRing {
 };
 
 template <int S>
-struct MMFromRing {
+struct MMFromRing : FusedStash {
     using T = typename Pack4<S>::T;
     const T* plane[3];  // slots of planes z - 1, z, z + 1
     int nxy;
@@ -466,6 +473,8 @@ struct MMFromRing {
 template <int S, int M>
 __global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA, StepArgs aB, FusedArgs F) {
     using T = typename Pack4<S>::T;
+    __shared__ float2 s_stash[12 * kBlock];  // the f^(1) halves, [velocity][compute thread]
+    const unsigned stash = fused_stash_slot(s_stash);
     const int nz = aA.g.nz, nxy = aA.g.nx * aA.g.ny;
     auto slot = [&](int p) -> T* {
         if (p == 0) return static_cast<T*>(F.lo);
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA
     fused_loop(F, aA.g.nx, nxy, nz, describe, [&](const FusedDesc& d) {
         const int p = d.plane, j = d.j, base = p * nxy;
         if (d.type == kPhaseA) {
-            const MMToRing<S> io{static_cast<T*>(d.ptr[0]), base, nxy};
+            const MMToRing<S> io{{stash}, static_cast<T*>(d.ptr[0]), base, nxy};
             if (j < F.tiles) {
                 const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
                 for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
@@ -494,7 +503,8 @@ __global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA
                     mm_update<S, M, true, false, false>(aA, aA.sv.cell[m], m, io);
             }
         } else {
-            const MMFromRing<S> io{{static_cast<const T*>(d.ptr[0]), static_cast<const T*>(d.ptr[1]),
+            const MMFromRing<S> io{{stash},
+                                   {static_cast<const T*>(d.ptr[0]), static_cast<const T*>(d.ptr[1]),
                                     static_cast<const T*>(d.ptr[2])},
                                    nxy};
             if (j < F.tiles) {
