@@ -135,10 +135,11 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m, const
     float4 e[6];
     float2 hy[6];
     io.template pull<S>(a, h, e, hy);
-    if constexpr (IO::kStash)  // the h pairs wait in shared memory until the collision
+    if constexpr (IO::kStash)  // the h components wait in shared memory until the collision
         static_for<0, 6>([&](auto ic) {
             constexpr int k = decltype(ic)::value;
             io.stash_put(k, hy[k].x, hy[k].y);
+            io.stash_put(6 + k, e[k].w, 0.f);  // h_x, which shares the float4 with e
         });
     const MatCoef mat = load_coef<kModelHV, M>(a.media, i, a.eps0, a.mu0);
     CellSource cs;
@@ -162,9 +163,13 @@ __device__ __forceinline__ void hv_update(const StepArgs& a, int i, int m, const
         if constexpr (A == 0) eo.x -= 0.5f * F.J.x;
         else if constexpr (A == 1) eo.y -= 0.5f * F.J.y;
         else eo.z -= 0.5f * F.J.z;
-        float hyx = hy[k].x, hyy = hy[k].y;
-        if constexpr (IO::kStash) io.stash_get(k, hyx, hyy);
-        float3 ho = make_float3(p.x + vE.x - e[k].w, p.y + vE.y - hyx, p.z + vE.z - hyy);
+        float hx = e[k].w, hyx = hy[k].x, hyy = hy[k].y;
+        if constexpr (IO::kStash) {
+            float unused;
+            io.stash_get(k, hyx, hyy);
+            io.stash_get(6 + k, hx, unused);
+        }
+        float3 ho = make_float3(p.x + vE.x - hx, p.y + vE.y - hyx, p.z + vE.z - hyy);
         if constexpr (kSpecial) {
             if (cs.imposed) {  // Appendix B "impose fields": f' = f_eq(E_imp, B_imp, J = 0)
                 const float3 cH = axis_cross<A, G>(hv_h(cs.B, mat));
@@ -243,7 +248,7 @@ template <int S, int M>
 __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA, StepArgs aB, FusedArgs F) {
     using T4 = typename Pack4<S>::T;
     using T2 = typename Pack2<S>::T;
-    __shared__ float2 s_stash[6 * kBlock];  // the h pairs, [velocity][compute thread]
+    __shared__ float2 s_stash[12 * kBlock];  // the h components, [slot][compute thread]
     const unsigned stash = fused_stash_slot(s_stash);
     const int nz = aA.g.nz, nxy = aA.g.nx * aA.g.ny;
     auto slot = [&](int p) -> T4* {
