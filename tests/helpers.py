@@ -29,19 +29,6 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a - b))
 
 
-def operator_matrix(L):
-    """The oracle's one-step map as a dense matrix, column c = step(unit vector c)."""
-    n = L.n * L.q
-    G = np.zeros((n, n))
-    for c in range(n):
-        u = np.zeros(n)
-        u[c] = 1.0
-        L.set_populations(u.reshape(L.q, L.n), 0)
-        L.step(1)
-        G[:, c] = L.populations().reshape(-1)
-    return G
-
-
 def peak_interp(y):
     """Signed value at the largest |y| sample, refined by a parabola through its two neighbours."""
     i = int(np.argmax(np.abs(y)))
