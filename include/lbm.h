@@ -37,7 +37,7 @@ enum {
     LBM_ENOMEM = -2,       /* device or host allocation failed */
     LBM_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
     LBM_ENONFINITE = -4,   /* lbm_check_finite found a NaN or infinity */
-    LBM_ETIMEDOUT = -5,    /* reserved for bounded waits */
+    LBM_ETIMEDOUT = -5,    /* a bounded wait ran out (a two-step pass's dependency wait) */
     LBM_EUNSUPPORTED = -6  /* valid request this build does not implement */
 };
 
@@ -188,10 +188,15 @@ int lbm_check_finite(lbm_ctx* ctx);
  * library holds until exit (4096 slots of 3 doubles, 96 KiB). It calls no cudaMalloc or cudaFree.
  *   out: 3 doubles. on_device = 1: device memory, written in stream order (no wait).
  *        on_device = 0: host memory; the call waits for the stream.
- * Limit: the lattice's reduction blocks (at most 608) plus one block per 256 source cells must fit
- *   in the 4096 slots; otherwise LBM_EINVAL with a message giving the limit.
+ * Limit: the lattice's reduction blocks (at most 608), plus for MM one block per 256 source cells
+ *   (about 890,000 source cells on a large lattice), must fit in the 4096 slots; otherwise
+ *   LBM_EINVAL with a message giving the limit. HV has no per-source-cell slots.
+ * With host output the call first reports, like lbm_reduce, a two-step pass whose dependency wait
+ *   ran out (LBM_ETIMEDOUT).
  * The first call on a device looks up the static array's device address (cudaGetSymbolAddress);
- *   make that first call before any stream capture. Every call, from any context, shares the one
+ *   make that first call before any stream capture. The address is kept for the life of the
+ *   process: after cudaDeviceReset (or anything else that unloads the library's module from the
+ *   device) later calls on that device are invalid. Every call, from any context, shares the one
  *   array: nothing in it needs to start at zero, but calls whose kernels overlap on the GPU (for
  *   instance two contexts on different streams) race on it, so order them on one stream or wait in
  *   between. */
@@ -220,12 +225,21 @@ int lbm_destroy(lbm_ctx* ctx);
  *   cells per SM (with 16-bit storage the single-step kernels are faster on GB300);
  *   2: whenever a plane has that many cells.
  * Never for z_ghost slabs or track_rho contexts, nor with nz < 4 (MM) or 5 (HV). The pass's dependency waits are
- * bounded (2 s); if one expires the pass stops, and the next lbm_sync, lbm_reduce or host-side
- * lbm_fields / lbm_get_populations returns LBM_ECUDA. Odd n ends with one single step. The pass
+ * bounded (2 s, lbm_set_wait_limit); if one expires every block of the pass stops, the populations
+ * of that pass are undefined, and the next lbm_sync, lbm_reduce, lbm_reduce_noalloc or host-side
+ * lbm_fields / lbm_get_populations returns LBM_ETIMEDOUT (once; until then later passes stop
+ * too). After that, restoring populations with lbm_set_populations makes the context usable
+ * again. Odd n ends with one single step. The pass
  * allocates its intermediate planes and counters on first use (kept until lbm_destroy).
  * tile_cells: cells per work item of a pass, a multiple of 256 up to 4096; 0 keeps the current
  * value (default 256 for MM, 512 for HV, the fastest on GB300). */
 int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells);
+/* Limit of each dependency wait of a two-step pass, in nanoseconds: ns > 0 sets it, ns == 0 restores
+ * the default of 2 s. ns < 0 makes every item of a pass that depends on another give up at its
+ * first check, whether its inputs are there or not, so that a test can drive the time-out path
+ * deterministically: the pass stops and the next waiting call returns LBM_ETIMEDOUT. Takes effect
+ * from the next pass. */
+int lbm_set_wait_limit(lbm_ctx* ctx, long long ns);
 /* 1 when lbm_step would run pairs of steps as single passes, 0 when not (negative on error). */
 int lbm_step_fusion_active(lbm_ctx* ctx);
 /* Self-check of the two-step pass's work order on the host, with the kernel's own order and tile
@@ -247,12 +261,15 @@ int lbm_fused_schedule_check(int nx, int ny, int nz, int R, int L, int tile_cell
  * every cell (n floats each; NULL skips one) are taken at fixed starting populations. The adjoint
  * steps back through the transposed collide-and-stream map. What it needs of forward step t is a
  * per-cell record: E and X = D' - mu0 J_ext / 4 for MM (24 bytes per cell), E for HV (12 bytes).
- *   checkpoint_interval < 0: the forward pass keeps every step's record in device memory
- *     (steps x record bytes); the backward pass recomputes nothing.
- *   checkpoint_interval > 0: population states are kept every checkpoint_interval steps, and each
- *     segment is recomputed once, writing its records, before it is stepped back through.
- *   checkpoint_interval == 0: the first mode when the records take at most half the free device
- *     memory, else the second with interval ceil(sqrt(steps)).
+ * The steps are cut into segments of K = checkpoint_interval steps, counted from the end (the first
+ * segment may be shorter). The forward pass writes the records of the final segment and keeps the
+ * population state at the start of every earlier one; going backward, each earlier segment is
+ * recomputed once from its state, writing its records, before it is stepped back through. Work
+ * space: K records + one state per earlier segment + 4 states.
+ *   checkpoint_interval < 0 (or >= steps): K = steps, every record resident, nothing recomputed.
+ *   checkpoint_interval > 0: that K.
+ *   checkpoint_interval == 0: resident when its work space fits in half the free device memory,
+ *     else K = lbm_adjoint_sqrt_interval(ctx, steps).
  * Every mode gives the same loss and gradients, bit for bit. Needs FP32 storage; source cells must
  * not lie in the plane (LBM_EINVAL). loss_out is a host double; gradient outputs are host
  * (on_device = 0) or device memory. The work space (records or checkpoints, two adjoint states, the
@@ -265,6 +282,12 @@ int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_index, int ch
 int lbm_adjoint_release(lbm_ctx* ctx);
 /* Bytes of device memory held as lbm_adjoint work space (0 when none; -1 for NULL). */
 int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx);
+/* Segment length of the checkpointed mode for `steps` steps: the longest K whose work space stays
+ * within that of the classic sqrt(T) layout (ceil(sqrt(steps)) states and as many records), so the
+ * memory grows like sqrt(steps). A record (24 B per cell MM, 12 B HV) is 8 (MM) or 12 (HV) times
+ * smaller than a state, so this K is several times sqrt(steps), and the forward pass records that
+ * many final steps instead of recomputing them. LBM_EINVAL (negative) for bad arguments. */
+int lbm_adjoint_sqrt_interval(const lbm_ctx* ctx, int steps);
 
 /* ---------------------------------------------------------------------------------------------
  * z-slab decomposition. The scheme couples a cell only to its 3 x 3 x 3 neighbourhood (Sections II

@@ -88,6 +88,7 @@ struct lbm_ctx {
     int plane_special_version = -1;
     int sources_version = 0;
     int fused_pending = 0;         // a pass ran since the abort flag was last read
+    long long wait_limit_ns = 0;   // dependency-wait limit of a pass (0: the default)
     std::vector<int> h_cell;       // host copy of the special-cell list (sorted)
     int64_t t = 0;
     int64_t launches = 0;
@@ -334,7 +335,7 @@ int fused_pass(lbm_ctx* c) {
     F.fix_flag = c->fused_ctrl + 2 + 2 * nz;
     F.tile_flag = c->fused_ctrl + 2 + 4 * nz;
     F.plane_special = c->d_plane_special;
-    F.timeout_ns = kFusedTimeoutNs;
+    F.timeout_ns = c->wait_limit_ns ? c->wait_limit_ns : kFusedTimeoutNs;
     CUDA_TRY(c, cudaMemsetAsync(c->fused_ctrl, 0, sizeof(int) * (1 + 2 * (size_t)nz), c->stream));
     const int launched = c->model == LBM_MM ? mm_launch_fused2(aA, aB, F, c->stream) : hv_launch_fused2(aA, aB, F, c->stream);
     int rc = check_launch(c, launched);
@@ -355,7 +356,9 @@ int check_fused_abort(lbm_ctx* c) {
     c->fused_pending = 0;
     if (flag) {
         CUDA_TRY(c, cudaMemsetAsync(abort, 0, sizeof(int), c->stream));
-        return fail(c, LBM_ECUDA, "a two-step pass stopped: a dependency wait exceeded its time limit");
+        return fail(c, LBM_ETIMEDOUT,
+                    "a two-step pass stopped: a dependency wait exceeded its time limit; the populations "
+                    "of that pass are undefined (restore them with lbm_set_populations)");
     }
     return LBM_OK;
 }
@@ -949,6 +952,12 @@ int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells) {
     return LBM_OK;
 }
 
+int lbm_set_wait_limit(lbm_ctx* ctx, long long ns) {
+    if (!ctx) return LBM_EINVAL;
+    ctx->wait_limit_ns = ns;
+    return LBM_OK;
+}
+
 int lbm_step_fusion_active(lbm_ctx* ctx) {
     if (!ctx) return LBM_EINVAL;
     int rc;
@@ -1073,12 +1082,19 @@ extern "C" int lbm_reduce_noalloc(lbm_ctx* ctx, double* out, int on_device) {
     if (!out) return fail(ctx, LBM_EINVAL, "lbm_reduce_noalloc: out is NULL");
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
-    const int ns_blocks = ctx->n_special > 0 ? (ctx->n_special + kBlock - 1) / kBlock : 0;
+    // Host output reports a two-step pass that stopped, as lbm_reduce does; device output is
+    // stream-ordered and leaves that to the next waiting call.
+    if (!on_device && (rc = check_fused_abort(ctx)) != LBM_OK) return rc;
+    // Only the MM reduction keeps one partial per 256 source cells: its energy takes a correction
+    // at source cells, where J_ext enters E. HV's E does not depend on J_ext, so it needs the
+    // lattice's blocks alone.
+    const int ns_blocks =
+        ctx->model == LBM_MM && ctx->n_special > 0 ? (ctx->n_special + kBlock - 1) / kBlock : 0;
     const int needed = ctx->reduce_blocks + ns_blocks;
     if (needed > kStaticPartialBlocks)
         return fail(ctx, LBM_EINVAL,
                     "lbm_reduce_noalloc: needs %d partial-sum slots but the static scratch holds %d "
-                    "(%d source cells is more than the %d it allows for this lattice)",
+                    "(%d source cells is more than the %d it allows for this MM lattice)",
                     needed, kStaticPartialBlocks, ctx->n_special, (kStaticPartialBlocks - ctx->reduce_blocks) * kBlock);
     double* scratch = nullptr;
     if ((rc = static_scratch(ctx, &scratch)) != LBM_OK) return rc;
@@ -1479,6 +1495,79 @@ int plane_size(const lbm_ctx* c, int axis) {
     return axis == 0 ? c->g.ny * c->g.nz : (axis == 1 ? c->g.nx * c->g.nz : c->g.nx * c->g.ny);
 }
 
+size_t record_bytes(const lbm_ctx* c) {
+    return sizeof(float) * (size_t)c->g.n * (c->model == LBM_MM ? kRecordFloatsMM : kRecordFloatsHV);
+}
+
+// Work space of the adjoint: K record slots, n_ck checkpoint states (plus two scratch states to
+// recompute through), two adjoint states, the gradient sums, the source-cell mask and the plane's
+// loss slots. Returns its size; with a base, sets the pieces' addresses.
+struct Layout {
+    char *recs, *ck, *work, *nu, *mask, *loss;
+    float *g_eps, *g_sig;
+};
+size_t adjoint_layout(const lbm_ctx* c, char* base, int K, int n_ck, int n_plane, Layout* L) {
+    const size_t n = (size_t)c->g.n;
+    const size_t state = (group_bytes(c->model, c->storage) + (c->model == LBM_HV ? pair_bytes(c->storage) : 0)) * n;
+    Arena a;
+    a.base = base;
+    L->recs = a.take(record_bytes(c) * (size_t)K);
+    L->ck = a.take(state * (size_t)n_ck);
+    L->work = a.take(n_ck > 0 ? state * 2 : 0);
+    L->nu = a.take(state * 2);
+    L->g_eps = reinterpret_cast<float*>(a.take(sizeof(float) * n));
+    L->g_sig = reinterpret_cast<float*>(a.take(sizeof(float) * n));
+    L->mask = a.take(n);
+    L->loss = a.take(sizeof(double) * ((size_t)n_plane + 3));
+    return a.used;
+}
+
+// Segment length K (the final segment's records come from the forward pass) and the number of
+// earlier segments, each recomputed once from a checkpoint.
+struct AdjointPlan {
+    int K, n_ck;
+};
+int earlier_segments(int steps, int K) { return K >= steps ? 0 : (steps - K + K - 1) / K; }
+
+// Largest segment length whose work space fits in `budget` bytes (0 when none does).
+int longest_fitting(const lbm_ctx* c, int steps, size_t budget) {
+    Layout L;
+    int best = 0;
+    for (int K = 1; K <= steps; ++K)
+        if (adjoint_layout(c, nullptr, K, earlier_segments(steps, K), 1, &L) <= budget) best = K;
+    return best;
+}
+
+// The checkpointed mode's segment length for `steps` steps: the longest whose work space stays
+// within that of ceil(sqrt(steps)) checkpoints and as many records, the classic sqrt(T) layout.
+// Its memory grows like sqrt(T); the longer final segment, recorded by the forward pass, spares
+// that many recomputed steps.
+int sqrt_interval(const lbm_ctx* c, int steps) {
+    const int k0 = std::max(1, (int)std::ceil(std::sqrt((double)steps)));
+    Layout L;
+    const size_t classic = adjoint_layout(c, nullptr, k0, (steps + k0 - 1) / k0, 1, &L);
+    return std::max(k0, longest_fitting(c, steps, classic));
+}
+
+// interval < 0: every record resident (K = steps); > 0: that segment length; 0: resident when its
+// work space fits in half the free memory, else the sqrt(T) layout.
+AdjointPlan adjoint_plan(const lbm_ctx* c, int steps, int interval) {
+    int K = steps;
+    if (interval > 0) {
+        K = std::min(interval, steps);
+    } else if (interval == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            free_b = 0;
+        }
+        Layout L;
+        const size_t avail = free_b + c->adj_ws_bytes;
+        if (adjoint_layout(c, nullptr, steps, 0, 1, &L) > avail / 2) K = sqrt_interval(c, steps);
+    }
+    return AdjointPlan{K, earlier_segments(steps, K)};
+}
+
 }  // namespace
 
 extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_index, int checkpoint_interval,
@@ -1501,44 +1590,17 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
         }
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
-    const int64_t n = ctx->g.n;
-    const size_t b1 = group_bytes(ctx->model, ctx->storage) * (size_t)n;
-    const size_t b2 = ctx->model == LBM_HV ? pair_bytes(ctx->storage) * (size_t)n : 0;
-    const size_t state = b1 + b2;
-    const size_t rec_bytes = sizeof(float) * (size_t)n * (ctx->model == LBM_MM ? kRecordFloatsMM : kRecordFloatsHV);
     const int n_plane = plane_size(ctx, plane_axis);
-    // Work space of a layout with K record slots and n_ck checkpoints (K = steps, n_ck = 0: resident).
-    struct Layout {
-        char *recs, *ck, *work, *nu, *mask, *loss;
-        float *g_eps, *g_sig;
-    };
-    auto layout = [&](char* base, int K, int n_ck, Layout* L) {
-        Arena a;
-        a.base = base;
-        L->recs = a.take(rec_bytes * (size_t)K);
-        L->ck = a.take(state * (size_t)n_ck);
-        L->work = a.take(n_ck > 0 ? state * 2 : 0);
-        L->nu = a.take(state * 2);
-        L->g_eps = reinterpret_cast<float*>(a.take(sizeof(float) * (size_t)n));
-        L->g_sig = reinterpret_cast<float*>(a.take(sizeof(float) * (size_t)n));
-        L->mask = a.take((size_t)n);
-        L->loss = a.take(sizeof(double) * ((size_t)n_plane + 3));
-        return a.used;
-    };
-    // Mode: every step's record resident in device memory (no recomputation) when asked for
-    // (interval < 0) or, automatically (interval == 0), when that work space fits in half the free
-    // memory; otherwise checkpoints of the state every K steps and one recomputation per segment.
-    size_t free_b = 0, total_b = 0;
-    CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
-    const size_t avail = free_b + ctx->adj_ws_bytes;
+    // The T steps are cut into segments from the end: a final segment of K steps, whose records the
+    // forward pass writes directly, and before it n_ck segments of K steps (the first one shorter)
+    // whose starting states the forward pass keeps as checkpoints. Going backward, each earlier
+    // segment is recomputed once from its checkpoint, writing its records into the same K slots.
+    // K = steps keeps every record and recomputes nothing (the resident mode).
+    const AdjointPlan plan = adjoint_plan(ctx, steps, checkpoint_interval);
+    const bool resident = plan.K == steps;
+    const int K = plan.K, n_ck = plan.n_ck;
     Layout Ly;
-    const size_t resident_bytes = layout(nullptr, steps, 0, &Ly);
-    const bool resident = checkpoint_interval < 0 || (checkpoint_interval == 0 && resident_bytes <= avail / 2);
-    const int K = resident ? steps
-                           : (checkpoint_interval > 0 ? checkpoint_interval
-                                                      : std::max(1, (int)std::ceil(std::sqrt((double)steps))));
-    const int n_ck = resident ? 0 : (steps + K - 1) / K;
-    const size_t need = layout(nullptr, K, n_ck, &Ly);
+    const size_t need = adjoint_layout(ctx, nullptr, K, n_ck, n_plane, &Ly);
     if (need > ctx->adj_ws_bytes) {
         CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         free_dev(ctx->adj_ws);
@@ -1551,7 +1613,12 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
         }
         ctx->adj_ws_bytes = need;
     }
-    layout(static_cast<char*>(ctx->adj_ws), K, n_ck, &Ly);
+    adjoint_layout(ctx, static_cast<char*>(ctx->adj_ws), K, n_ck, n_plane, &Ly);
+    const int64_t n = ctx->g.n;
+    const size_t b1 = group_bytes(ctx->model, ctx->storage) * (size_t)n;
+    const size_t b2 = ctx->model == LBM_HV ? pair_bytes(ctx->storage) * (size_t)n : 0;
+    const size_t state = b1 + b2;
+    const size_t rec_bytes = record_bytes(ctx);
     CUDA_TRY(ctx, cudaMemsetAsync(Ly.g_eps, 0, sizeof(float) * (size_t)n, ctx->stream));
     CUDA_TRY(ctx, cudaMemsetAsync(Ly.g_sig, 0, sizeof(float) * (size_t)n, ctx->stream));
     CUDA_TRY(ctx, cudaMemsetAsync(Ly.mask, 0, (size_t)n, ctx->stream));
@@ -1584,17 +1651,21 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
     };
     int64_t launched = 0;
     const int64_t t0 = ctx->t;
-    // Forward pass: records (resident mode) or checkpoints.
-    for (int s = 0; s < steps; ++s) {
+    const int final_first = steps - K;  // first step of the final segment
+    // first step of earlier segment k (0 .. n_ck - 1); segment k ends where k + 1 starts
+    auto seg_first = [&](int k) { return std::max(0, final_first - (n_ck - k) * K); };
+    // Forward pass: checkpoints at the start of every earlier segment, records of the final one.
+    for (int s = 0, next_ck = 0; s < steps; ++s) {
         void* in1 = ctx->buf[ctx->cur];
         void* in2 = ctx->buf2[ctx->cur];
-        if (!resident && s % K == 0) {
-            char* slot = Ly.ck + state * (size_t)(s / K);
+        if (next_ck < n_ck && s == seg_first(next_ck)) {
+            char* slot = Ly.ck + state * (size_t)next_ck;
             CUDA_TRY(ctx, cudaMemcpyAsync(slot, in1, b1, cudaMemcpyDeviceToDevice, ctx->stream));
             if (b2) CUDA_TRY(ctx, cudaMemcpyAsync(slot + b1, in2, b2, cudaMemcpyDeviceToDevice, ctx->stream));
+            ++next_ck;
         }
         launched += forward(in1, in2, ctx->buf[1 - ctx->cur], ctx->buf2[1 - ctx->cur], t0 + s + 1, true,
-                            resident ? Ly.recs + rec_bytes * (size_t)s : nullptr);
+                            s >= final_first ? Ly.recs + rec_bytes * (size_t)(s - final_first) : nullptr);
         ctx->cur = 1 - ctx->cur;
         ctx->t += 1;
     }
@@ -1621,12 +1692,13 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
     A.loss_active = 1;
     launched += ctx->model == LBM_MM ? mm_launch_adjoint_terminal(A, n_plane, ctx->stream)
                                      : hv_launch_adjoint_terminal(A, n_plane, ctx->stream);
-    // Backward through one run of records (those of steps first .. first + len - 1).
+    // Backward through the segment of steps first .. first + len - 1, whose records are in slots
+    // 0 .. len - 1.
     auto backward = [&](int first, int len) {
         for (int j = len - 1; j >= 0; --j) {
             const int64_t nstep = first + j;  // reverses forward iteration nstep + 1
             A.a = base_args(ctx);
-            A.a.rec = reinterpret_cast<float*>(Ly.recs + rec_bytes * (size_t)(resident ? nstep : j));
+            A.a.rec = reinterpret_cast<float*>(Ly.recs + rec_bytes * (size_t)j);
             fill_scalars(ctx, A.a, t0 + nstep + 1);
             state_ptrs(Ly.nu + state * (size_t)nu_cur, const_cast<void**>(&A.nu_in), const_cast<void**>(&A.nu_in2));
             state_ptrs(Ly.nu + state * (size_t)(1 - nu_cur), &A.nu_out, &A.nu_out2);
@@ -1635,22 +1707,19 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
             nu_cur = 1 - nu_cur;
         }
     };
-    if (resident) {
-        backward(0, steps);
-    } else {
-        for (int k = n_ck - 1; k >= 0; --k) {
-            const int first = k * K, len = std::min(K, steps - first);
-            // Recompute the segment from its checkpoint through two scratch states, recording each step.
-            void *i1, *i2, *o1, *o2;
-            state_ptrs(Ly.ck + state * (size_t)k, &i1, &i2);
-            for (int j = 0; j < len; ++j) {
-                state_ptrs(Ly.work + state * (size_t)(j & 1), &o1, &o2);
-                launched += forward(i1, i2, o1, o2, t0 + first + j + 1, false, Ly.recs + rec_bytes * (size_t)j);
-                i1 = o1;
-                i2 = o2;
-            }
-            backward(first, len);
+    backward(final_first, K);
+    for (int k = n_ck - 1; k >= 0; --k) {
+        const int first = seg_first(k), len = (k + 1 < n_ck ? seg_first(k + 1) : final_first) - first;
+        // Recompute the segment from its checkpoint through two scratch states, recording each step.
+        void *i1, *i2, *o1, *o2;
+        state_ptrs(Ly.ck + state * (size_t)k, &i1, &i2);
+        for (int j = 0; j < len; ++j) {
+            state_ptrs(Ly.work + state * (size_t)(j & 1), &o1, &o2);
+            launched += forward(i1, i2, o1, o2, t0 + first + j + 1, false, Ly.recs + rec_bytes * (size_t)j);
+            i1 = o1;
+            i2 = o2;
         }
+        backward(first, len);
     }
     launched += launch_sum_doubles(loss_plane, n_plane, loss_dev, ctx->stream);
     if ((rc = check_launch(ctx, (int)launched)) != LBM_OK) return rc;
@@ -1676,6 +1745,11 @@ extern "C" int lbm_adjoint_release(lbm_ctx* ctx) {
 }
 
 extern "C" int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx) { return ctx ? (int64_t)ctx->adj_ws_bytes : -1; }
+
+extern "C" int lbm_adjoint_sqrt_interval(const lbm_ctx* ctx, int steps) {
+    if (!ctx || steps < 1) return LBM_EINVAL;
+    return sqrt_interval(ctx, steps);
+}
 
 // ------------------------------------------------------------------------------------------------
 // z-slab halo: pack, unpack and exchange of the populations that cross a z face.

@@ -522,7 +522,9 @@ __device__ __forceinline__ void add_plane_loss(const AdjointArgs& A, const Neigh
 //     slot's previous plane, p - R;
 //   * a source-cell item waits for every tile of its own phase.
 // Tiles publish the pass number in a flag of their own, so the flags need no reset between passes.
-// Every wait has a time limit; past it the pass sets `abort` and every block stops.
+// Every wait has a time limit; past it the pass sets `abort` and every block stops. A negative
+// limit makes every item that depends on another give up at its first check, met or not: the host
+// uses it to drive the time-out path deterministically in tests.
 struct FusedArgs {
     void* ring;   // R slots of one plane of intermediate populations (the model's group layout)
     void* lo;     // slot of plane 0
@@ -541,7 +543,7 @@ struct FusedArgs {
     int* fix_flag;              // 2 nz source-cell item flags, A then B
     int* abort;                 // set when a wait timed out
     const int* plane_special;   // nz + 1 offsets of each plane's cells in the special-cell list
-    long long timeout_ns;
+    long long timeout_ns;       // < 0: give up at the first dependency check
 };
 
 enum { kPhaseA = 0, kPhaseB = 1 };
@@ -659,7 +661,12 @@ __device__ inline bool fused_ready_warp(const FusedArgs& F, int nz, FusedItem it
     bool ok = true;
     // one look (wait == false) or a bounded wait
     auto reached = [&](const int* p, int target) { return wait ? fused_wait(F, p, target) : load_acquire(p) >= target; };
+    auto give_up = [&]() {  // negative limit: stop the pass at the first item with a dependency
+        if (lane == 0) atomicExch(F.abort, 1);
+        return false;
+    };
     if (it.j == F.tiles) {  // source-cell item: every tile of its own phase
+        if (F.timeout_ns < 0) return give_up();
         const bool own_tile = own.type == it.type && own.plane == it.plane && own.j < F.tiles;
         if (lane == 0) ok = reached(F.count + it.type * nz + it.plane, F.tiles - (own_tile ? 1 : 0));
         return __all_sync(0xffffffffu, ok);
@@ -667,6 +674,7 @@ __device__ inline bool fused_ready_warp(const FusedArgs& F, int nz, FusedItem it
     int q[3];
     int wtype = 0;
     if (fused_waits_on(it.type, it.plane, nz, F.R, &wtype, q) == 0) return true;
+    if (F.timeout_ns < 0) return give_up();
     int first, count;
     tile_window(it.j, F.tiles, F.tile_cells, nx, nxy, &first, &count);
     for (int idx = lane; ok && idx < 3 * count; idx += 32) {

@@ -96,12 +96,14 @@ def load_library(path: str | None = None):
         "lbm_adjoint_release": (I, [P]),
         "lbm_set_step_fusion": (I, [P, I, I]),
         "lbm_step_fusion_active": (I, [P]),
+        "lbm_set_wait_limit": (I, [P, ctypes.c_longlong]),
         "lbm_fused_schedule_check": (I, [I, I, I, I, I, I]),
         "lbm_halo_bytes": (I64, [P]),
         "lbm_halo_pack": (I, [P, I, P, I]),
         "lbm_halo_unpack": (I, [P, I, P, I]),
         "lbm_halo_exchange": (I, [P, P]),
         "lbm_adjoint_workspace_bytes": (I64, [P]),
+        "lbm_adjoint_sqrt_interval": (I, [P, I]),
         "lbm_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P)]),
         "lbm_batch_step": (I, [P, ctypes.POINTER(I)]),
         "lbm_batch_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -323,8 +325,10 @@ class Lattice:
     def adjoint(self, steps: int, plane_axis: int, plane_index: int, checkpoint_interval: int = 0):
         """Advance `steps` steps and return (L, dL/d eps_r, dL/d sigma) for the plane loss
         L = sum_t sum_plane |E(t)|^2 (lbm_adjoint); gradients are torch CUDA tensors (n,).
-        checkpoint_interval: < 0 keeps every step's record on the device, > 0 checkpoints the state
-        that often, 0 picks the first when it fits in half the free memory, else sqrt(steps)."""
+        checkpoint_interval: the segment length K. < 0 keeps every step's record on the device; > 0
+        records the final K steps in the forward pass and recomputes each earlier K-step segment
+        once from a checkpoint; 0 picks the first when it fits in half the free memory, else
+        K = sqrt_interval(steps)."""
         import torch
         ge = torch.empty(self.n, dtype=torch.float32, device=self.device)
         gs = torch.empty(self.n, dtype=torch.float32, device=self.device)
@@ -341,6 +345,11 @@ class Lattice:
         planes fit in L2; 2: whenever the lattice allows it. tile_cells: cells per work item of a
         pass (multiple of 256; 0 keeps the current value) (lbm_set_step_fusion)."""
         self._check(self.lib.lbm_set_step_fusion(self.h, int(mode), int(tile_cells)))
+
+    def set_wait_limit(self, ns: int) -> None:
+        """Limit of each dependency wait of a two-step pass in nanoseconds; 0 restores the default
+        (2 s); negative: every dependent item gives up at once, for tests (lbm_set_wait_limit)."""
+        self._check(self.lib.lbm_set_wait_limit(self.h, int(ns)))
 
     @property
     def step_fusion_active(self) -> bool:
@@ -386,6 +395,14 @@ class Lattice:
     @property
     def adjoint_workspace_bytes(self) -> int:
         return int(self.lib.lbm_adjoint_workspace_bytes(self.h))
+
+    def sqrt_interval(self, steps: int) -> int:
+        """Segment length of the checkpointed adjoint for `steps` steps: the longest within the work
+        space of the classic sqrt(T) layout (lbm_adjoint_sqrt_interval)."""
+        k = int(self.lib.lbm_adjoint_sqrt_interval(self.h, int(steps)))
+        if k < 0:
+            self._check(k)
+        return k
 
     def check_finite(self) -> bool:
         rc = self.lib.lbm_check_finite(self.h)

@@ -52,7 +52,7 @@ def gpu_adjoint(w, f0, steps, plane, interval=0, t0=3):
 def test_adjoint_matches_oracle_adjoint(model):
     w, f0, plane = small_case(model)
     steps = 20
-    L, loss, ge, gs = gpu_adjoint(w, f0, steps, plane, interval=6)  # segments 6, 6, 6, 2
+    L, loss, ge, gs = gpu_adjoint(w, f0, steps, plane, interval=6)  # segments 2, 6, 6 and the final 6
     O = oracle_from_workload(w, init=False, threads=8)
     O.set_populations(f0, 3)
     loss_ref, ge_ref, gs_ref = O.loss_and_gradient(steps, *plane)
@@ -71,7 +71,7 @@ def test_checkpoint_interval_does_not_change_the_result(model):
     """Recomputation replays the same kernels on the same states: every checkpoint interval, and
     keeping every step's record resident (interval -1), gives the same loss and gradients bit for bit."""
     w, f0, plane = small_case(model, seed=82)
-    results = [gpu_adjoint(w, f0, 17, plane, interval=k)[1:] for k in (1, 3, 0, 17, -1)]
+    results = [gpu_adjoint(w, f0, 17, plane, interval=k)[1:] for k in (1, 3, 5, 8, 16, 0, 17, 40, -1)]
     for loss, ge, gs in results[1:]:
         assert loss == results[0][0]
         assert np.array_equal(ge, results[0][1])
@@ -200,3 +200,30 @@ def test_adjoint_refuses_what_it_does_not_support(model):
     with pytest.raises(LbmError):
         S.adjoint(3, 0, 2)
     S.close()
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_sqrt_interval_stays_within_the_classic_sqrt_layout(model):
+    """The checkpointed mode's segment length is the longest whose work space does not exceed that
+    of ceil(sqrt(T)) checkpoints and as many records: at least ceil(sqrt(T)), a work space no larger
+    than the classic layout's, one step longer already over it, and the same result bit for bit."""
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    w, f0, plane = small_case(model, seed=88)
+    steps = 400  # long enough that keeping every record costs more than the classic layout
+    k0 = 20
+    L = lattice_from_workload(w, init=False)
+    K = L.sqrt_interval(steps)
+    assert k0 <= K < steps
+    held = {}
+    results = {}
+    for k in (k0, K, K + 1):
+        L.adjoint_release()
+        L.set_populations(np.asarray(f0, np.float32), 3)
+        loss, ge, gs = L.adjoint(steps, *plane, k)
+        held[k] = L.adjoint_workspace_bytes
+        results[k] = (loss, ge.cpu().numpy(), gs.cpu().numpy())
+    assert held[K] <= held[k0] < held[K + 1]
+    for k in (K, K + 1):
+        assert results[k][0] == results[k0][0]
+        assert np.array_equal(results[k][1], results[k0][1]) and np.array_equal(results[k][2], results[k0][2])
+    L.close()

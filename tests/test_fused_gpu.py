@@ -139,3 +139,51 @@ def test_fusion_mode_is_checked():
         with pytest.raises(LbmError):
             L.set_step_fusion(mode, tile)
     L.close()
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_expired_wait_stops_the_pass_and_reports_etimedout(model):
+    """A dependency wait that runs out stops every block of the pass, and the next waiting call
+    returns LBM_ETIMEDOUT once, naming the pass. A negative wait limit makes the first check of every
+    dependent item give up, so the path is taken on every run, without a fault or a hang. The
+    context then steps as before: restored populations give single steps' results bit for bit."""
+    from paper_2309_08068_gb300.lbm import LbmError, lattice_from_workload
+    w, f = wl.slab_case(model, PLANE + (7,), seed=140)
+    f = np.asarray(f, np.float32)
+    q = 48 if model == "mm" else 36
+    L = lattice_from_workload(w, init=False)
+    L.set_step_fusion(2)
+    assert L.step_fusion_active
+    L.set_populations(f, 0)
+    L.set_wait_limit(-1)
+    L.step(2)
+    with pytest.raises(LbmError) as err:
+        L.sync()
+    assert err.value.code == -5  # LBM_ETIMEDOUT
+    assert "two-step pass" in str(err.value)
+    L.sync()  # reported once
+    L.set_wait_limit(0)
+    L.set_populations(f, 0)
+    L.step(4)
+    fused = L.populations_host(), L.fields_host("EBJ"), L.time
+    L.close()
+    _, single = run(w, f, 4, 0)
+    assert_same(fused, single, q)
+
+
+def test_expired_wait_is_reported_by_host_reductions_and_reads():
+    """Every host-side read after a stopped pass reports it: lbm_reduce, lbm_get_populations and
+    lbm_fields return LBM_ETIMEDOUT instead of values of undefined populations."""
+    from paper_2309_08068_gb300.lbm import LbmError, lattice_from_workload
+    w, f = wl.slab_case("mm", PLANE + (6,), seed=141)
+    L = lattice_from_workload(w, init=False)
+    L.set_step_fusion(2)
+    L.set_populations(np.asarray(f, np.float32), 0)
+    for read in (L.reduce, L.populations_host, lambda: L.fields_host("E")):
+        L.set_wait_limit(-1)
+        L.step(2)
+        with pytest.raises(LbmError) as err:
+            read()
+        assert err.value.code == -5
+    L.set_wait_limit(0)
+    L.close()
