@@ -8,8 +8,11 @@ cells included). Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
 
 Under torchrun (N > 1) every rank runs its own pair of lattices (independent problems, weak
-scaling, no data-path collective); timing is the maximum over ranks. ``--impl reference`` times
-the FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+scaling, no data-path collective) by default. With ``--decomposition slabs`` the ranks instead split
+one lattice per model into N z-slabs, one per rank, and exchange one plane of populations per face
+and step with their neighbours (NCCL send/recv of packed faces; strong scaling). Timing is the
+maximum over ranks. ``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -249,8 +252,10 @@ def storage_accuracy(storages=("f32", "bf16", "f16")):
 
 def refinement_sweep(stream, steps: int):
     """The skin-effect mesh-refinement sweep (16 lattices N = 32 ... 272, 95.9 M cells, sigma = 0.1):
-    `steps` steps of every lattice, batched (one launch per step, captured graph, autotuned launch
-    configuration) against each lattice stepped on its own, same stream, same data."""
+    `steps` steps of every lattice, batched (lattices whose planes fill the GPU as two-step passes,
+    the others one launch per step, captured graph, autotuned launch configuration) against each
+    lattice stepped on its own, one launch per step (lbm_step(ctx, 1)) and in one call
+    (lbm_step(ctx, steps), two-step passes where they apply), same stream, same data."""
     import torch
     from paper_2309_08068_gb300.lbm import Batch, lattice_from_workload
     out = {}
@@ -281,9 +286,18 @@ def refinement_sweep(stream, steps: int):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_single = e0.elapsed_time(e1)
+        e0.record(stream)
+        for L in lats:
+            L.step(steps)  # lbm_step(ctx, steps): two-step passes where they apply
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_own = e0.elapsed_time(e1)
+        passes = [L.step_fusion_active for L in lats]
         out[model] = {"lattices": len(works), "cells": cells, "steps": steps,
+                      "lattices_with_two_step_pass": [w.shape[0] for w, a in zip(works, passes) if a],
                       "batched_graph_MLUPS": round(cells * steps / (ms_batched * 1e-3) / 1e6, 1),
                       "per_lattice_launches_MLUPS": round(cells * steps / (ms_single * 1e-3) / 1e6, 1),
+                      "per_lattice_lbm_step_MLUPS": round(cells * steps / (ms_own * 1e-3) / 1e6, 1),
                       "first_call_with_capture_ms": round(ms_capture, 2),
                       "autotuned": {"block": block, "persistent": persistent}}
         batch.close()
@@ -677,6 +691,136 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def time_slab_split(n_side: int, nz: int, steps: int, warmup: int, rank: int, world: int, stream):
+    """One n_side^2 x nz dipole lattice per model split into `world` z-slabs, slab `rank` on this
+    device: every step exchanges the halo with the neighbouring ranks (slabs.exchange: NCCL send and
+    receive of packed faces; a single slab closes the ring on itself), then steps the slab once.
+    Returns per-model step and exchange times (CUDA events on the slabs' stream, this rank) and the
+    bytes each rank sends per step."""
+    import torch
+    from paper_2309_08068_gb300.slabs import SlabRank
+    models = ("mm", "hv")
+    with torch.cuda.stream(stream):
+        parts = {m: SlabRank(wl.hertz_dipole(m, n=n_side, period=32.0, nz=nz), rank, world, stream=stream)
+                 for m in models}
+        for _ in range(warmup):
+            for m in models:
+                parts[m].step(1)
+        torch.cuda.synchronize()
+        events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        launches0 = sum(P.lattice.launch_count for P in parts.values())
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for ev in events:
+            ev[0].record(stream)
+            parts["mm"].step(1)
+            ev[1].record(stream)
+            parts["hv"].step(1)
+            ev[2].record(stream)
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t0
+        launches = sum(P.lattice.launch_count for P in parts.values()) - launches0
+        per_model = {m: sum(e[k].elapsed_time(e[k + 1]) for e in events) / steps for k, m in enumerate(models)}
+        elapsed_ms = events[0][0].elapsed_time(events[-1][2])
+        # the exchange alone, for the record
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(5, min(steps, 50))
+        exch = {}
+        for m in models:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(k):
+                parts[m].exchange()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            exch[m] = e0.elapsed_time(e1) / k
+        # end to end through the C ABI: the slab's fields from pinned host memory, the steps, E and B
+        # of the slab back to host memory
+        slab_n = parts["mm"].lattice.n
+        pinned = torch.zeros((3, slab_n), dtype=torch.float32).pin_memory()
+        host_out = np.empty((2, 3, slab_n), np.float32)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for P in parts.values():
+            P.lattice._check(P.lattice.lib.lbm_init_fields(P.lattice.h, pinned.data_ptr(), pinned.data_ptr(), 0))
+        for _ in range(steps):
+            for m in models:
+                parts[m].step(1)
+        for P in parts.values():
+            P.lattice._check(P.lattice.lib.lbm_fields(P.lattice.h, 3, host_out.ctypes.data, 0))
+        e2e_s = time.perf_counter() - t0
+    out = {"elapsed_ms": elapsed_ms, "wall_s": wall_s, "launches": launches, "per_model_ms": per_model,
+           "e2e_s": e2e_s, "e2e_bytes": 2 * 2 * 3 * slab_n * 4,
+           "exchange_ms": exch, "slab_planes": parts["mm"].bounds,
+           "halo_bytes_sent_per_step": {m: 2 * P.lattice.halo_bytes for m, P in parts.items()},
+           "finite": all(P.lattice.check_finite() for P in parts.values())}
+    for P in parts.values():
+        P.close()
+    return out
+
+
+def run_slabs(args):
+    """--decomposition slabs under torchrun with N > 1: one lattice per model split across the ranks
+    (strong scaling); rank 0 prints the line."""
+    import torch
+    import torch.distributed as dist
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    n_side = args.n
+    nz = args.nz or n_side
+    ncell = n_side * n_side * nz
+    stream = torch.cuda.Stream()
+    with ClockSampler(local) as clocks:
+        res = time_slab_split(n_side, nz, args.steps, args.warmup, rank, world, stream)
+    elapsed_ms = max_over_ranks(res["elapsed_ms"], world)
+    mm_ms = max_over_ranks(res["per_model_ms"]["mm"], world)
+    hv_ms = max_over_ranks(res["per_model_ms"]["hv"], world)
+    e2e_s = max_over_ranks(res["e2e_s"], world)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    peak, peak_kind = hbm_peak()
+    cells_rank = ncell // world
+    bpc = {m: BYTES_PER_CELL[m] for m in BYTES_PER_CELL}
+    cores = cpu_cores()
+    cpu_mlups, cpu_steps, cpu_s = oracle_mlups(64, args.cpu_seconds, cores)
+    line = {
+        "metric": METRIC, "value": round(2 * ncell * args.steps / (elapsed_ms * 1e-3) / 1e6, 2),
+        "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "storage": "f32", "data": "synthetic",
+        "config": {"workload": f"hertz_dipole_{n_side}x{n_side}x{nz}_mm+hv", "cells_per_model": ncell,
+                   "step": "per model: halo exchange with both neighbours, then one step of the rank's slab",
+                   "parallelism": f"z-slabs x{world} (one per rank), NCCL send/recv of packed faces",
+                   "slab_planes_rank0": res["slab_planes"],
+                   "l2": "inputs larger than L2 when the slab is"},
+        "per_model": {m: {"ms_per_step": round(t, 4), "MLUPS": round(ncell / (t * 1e-3) / 1e6, 2),
+                          "exchange_ms": round(res["exchange_ms"][m], 4),
+                          "halo_bytes_sent_per_rank_step": res["halo_bytes_sent_per_step"][m]}
+                      for m, t in (("mm", mm_ms), ("hv", hv_ms))},
+        "roofline": {"bound": "hbm", "kernel": "mm_step_kernel (one step per launch on each slab)",
+                     "achieved": round(bpc["mm"] * cells_rank / (mm_ms * 1e-3) / 1e9, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(bpc["mm"] * cells_rank / (mm_ms * 1e-3) / 1e9 / peak, 4),
+                     "traffic": None, "note": "per rank, exchange included in the step time"},
+        "cpu_baseline": {"value": round(cpu_mlups, 4), "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"64^3 dipole lattice per model, FP64, {cpu_steps} steps, {cpu_s:.1f} s"},
+        "e2e": {"value": round(2 * ncell * args.steps / e2e_s / 1e6, 2), "unit": "Mcell-updates/s",
+                "h2d_bytes_per_step": res["e2e_bytes"] * world // args.steps,
+                "d2h_bytes_per_step": res["e2e_bytes"] * world // args.steps,
+                "job": f"per rank: lbm_init_fields of its slab from pinned host E, B + {args.steps} steps with "
+                       "halo exchanges + lbm_fields E, B to host"},
+        "gpu_launches": int(res["launches"]),
+        "finite": res["finite"],
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def roofline_entry(model, kernel, fused, bytes_update, bytes_own, ncell, ms_per_step, peak, peak_kind, traffic):
     """Roofline of one model's step kernel. `achieved` and `frac` count the method's algorithmic
     bytes per cell update (populations read and written once per step: 384 B MM, 288 B HV in FP32)
@@ -726,6 +870,10 @@ def main():
                     help="steps of the batched refinement-sweep measurement (0 skips it)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="population storage of the main timed run (arithmetic is FP32 in every case)")
+    ap.add_argument("--decomposition", choices=["replicas", "slabs"], default="replicas",
+                    help="with N > 1 ranks: independent lattices per rank (replicas, weak scaling) or one "
+                         "lattice per model split into N z-slabs with a halo exchange every step (slabs, "
+                         "strong scaling). With one rank both are the unsplit lattice.")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -736,7 +884,10 @@ def main():
         build.build()
         import oracle
         oracle.build()
-        run_ours(args)
+        if args.decomposition == "slabs" and dist_info()[0] > 1:
+            run_slabs(args)
+        else:
+            run_ours(args)
 
 
 if __name__ == "__main__":

@@ -283,8 +283,8 @@ int lbm_adjoint_release(lbm_ctx* ctx);
 /* Bytes of device memory held as lbm_adjoint work space (0 when none; -1 for NULL). */
 int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx);
 /* Segment length of the checkpointed mode for `steps` steps: the longest K whose work space stays
- * within that of the classic sqrt(T) layout (ceil(sqrt(steps)) states and as many records), so the
- * memory grows like sqrt(steps). A record (24 B per cell MM, 12 B HV) is 8 (MM) or 12 (HV) times
+ * within that of segments of ceil(sqrt(steps)) steps (about sqrt(steps) states and as many
+ * records, the classic sqrt(T) layout), so the memory grows like sqrt(steps). A record (24 B per cell MM, 12 B HV) is 8 (MM) or 12 (HV) times
  * smaller than a state, so this K is several times sqrt(steps), and the forward pass records that
  * many final steps instead of recomputing them. LBM_EINVAL (negative) for bad arguments. */
 int lbm_adjoint_sqrt_interval(const lbm_ctx* ctx, int steps);
@@ -334,8 +334,10 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out);
 
 /* Advance context k by steps[k] >= 0 time steps (results identical, bit for bit, to lbm_step on each
- * context). Step j of the call updates every context with steps[k] > j in one launch (plus one launch
- * for source cells); each context's time and sources advance as in lbm_step. On a non-default stream the
+ * context). A context for which lbm_step would run two steps per pass (lbm_set_step_fusion) runs its
+ * steps exactly that way, through direct launches. Step j of the call updates every other context
+ * with steps[k] > j in one launch (plus one launch for source cells); each context's time and
+ * sources advance as in lbm_step. On a non-default stream the
  * whole call is captured once into a CUDA graph and replayed by later calls with the same steps,
  * sizes and source-cell counts; on the legacy default stream the launches are issued directly.
  * Asynchronous: enqueued on the contexts' stream. */

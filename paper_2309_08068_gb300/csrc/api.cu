@@ -82,10 +82,10 @@ struct lbm_ctx {
     int fused_tile = 0;            // cells per work item of a pass (0: the model's default)
     void* fused_planes = nullptr;  // R ring slots + the slots of planes 0 and nz - 1
     size_t fused_planes_bytes = 0;
-    int* fused_ctrl = nullptr;     // item counter, 2 nz tile counters, abort, 2 nz + 2 nz tiles flags
+    int* fused_ctrl = nullptr;     // item counter, abort, 2 nz tiles tile flags
     int fused_epoch = 0;           // number of the last pass launched
-    int* d_plane_special = nullptr;
-    int plane_special_version = -1;
+    int* d_tile_special = nullptr;  // nz tiles + 1 offsets of each tile's cells in the special-cell list
+    int tile_special_version = -1;   // sources_version it was built for (-1: rebuild)
     int sources_version = 0;
     int fused_pending = 0;         // a pass ran since the abort flag was last read
     long long wait_limit_ns = 0;   // dependency-wait limit of a pass (0: the default)
@@ -223,11 +223,11 @@ FusedShape fused_shape(const lbm_ctx* c) { return c->model == LBM_MM ? kFusedMM 
 int fused_tile_cells(const lbm_ctx* c) { return c->fused_tile ? c->fused_tile : fused_shape(c).tile; }
 int fused_tiles(const lbm_ctx* c) { return (c->g.nx * c->g.ny + fused_tile_cells(c) - 1) / fused_tile_cells(c); }
 
-// Pass control block: [item counter][2 nz tile counters][abort][2 nz source-item flags]
-// [2 nz x tiles tile flags]. The first 1 + 2 nz are zeroed before every pass.
+// Pass control block: [item counter][abort][2 nz x tiles tile flags]. The item counter is zeroed
+// before every pass; the abort flag stays set until check_fused_abort reports it.
 size_t fused_ctrl_ints(const lbm_ctx* c) {
     const size_t nz = (size_t)c->g.nz, tiles = (size_t)fused_tiles(c);
-    return 1 + 2 * nz + 1 + 2 * nz + 2 * nz * tiles;
+    return 2 + 2 * nz * tiles;
 }
 
 size_t fused_plane_bytes(const lbm_ctx* c) {
@@ -278,22 +278,26 @@ int ensure_fused(lbm_ctx* c) {
         CUDA_TRY(c, cudaMemsetAsync(c->fused_ctrl, 0, sizeof(int) * ints, c->stream));
         c->fused_epoch = 0;
     }
-    if (c->plane_special_version != c->sources_version || !c->d_plane_special) {
-        // offsets of each plane's cells in the sorted special-cell list
-        const int nz = c->g.nz, nxy = c->g.nx * c->g.ny;
-        std::vector<int> off((size_t)nz + 1, 0);
+    if (c->tile_special_version != c->sources_version || !c->d_tile_special) {
+        // offsets of each tile's cells in the sorted special-cell list: tile j of plane p holds cells
+        // p nxy + j tile_cells .. (up to the end of the plane)
+        const int nz = c->g.nz, nxy = c->g.nx * c->g.ny, tiles = fused_tiles(c), tc = fused_tile_cells(c);
+        std::vector<int> off((size_t)nz * tiles + 1, 0);
         size_t m = 0;
-        for (int p = 0; p <= nz; ++p) {
-            while (m < c->h_cell.size() && c->h_cell[m] < p * nxy) ++m;
-            off[(size_t)p] = (int)m;
+        for (size_t k = 0; k <= (size_t)nz * tiles; ++k) {
+            const int p = (int)(k / tiles), j = (int)(k % tiles);
+            const long long start = (long long)p * nxy + std::min((long long)j * tc, (long long)nxy);
+            while (m < c->h_cell.size() && c->h_cell[m] < start) ++m;
+            off[k] = (int)m;
         }
-        if (!c->d_plane_special && cudaMalloc(&c->d_plane_special, sizeof(int) * ((size_t)nz + 1)) != cudaSuccess) {
+        free_dev(c->d_tile_special);
+        if (cudaMalloc(&c->d_tile_special, sizeof(int) * off.size()) != cudaSuccess) {
             cudaGetLastError();
-            c->d_plane_special = nullptr;
-            return fail(c, LBM_ENOMEM, "lbm_step: cannot allocate the plane offsets");
+            c->d_tile_special = nullptr;
+            return fail(c, LBM_ENOMEM, "lbm_step: cannot allocate the tiles' source-cell offsets");
         }
-        CUDA_TRY(c, cudaMemcpy(c->d_plane_special, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
-        c->plane_special_version = c->sources_version;
+        CUDA_TRY(c, cudaMemcpy(c->d_tile_special, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+        c->tile_special_version = c->sources_version;
     }
     return LBM_OK;
 }
@@ -330,13 +334,11 @@ int fused_pass(lbm_ctx* c) {
     F.tiles = fused_tiles(c);
     F.epoch = ++c->fused_epoch;
     F.next = c->fused_ctrl;
-    F.count = c->fused_ctrl + 1;
-    F.abort = c->fused_ctrl + 1 + 2 * nz;
-    F.fix_flag = c->fused_ctrl + 2 + 2 * nz;
-    F.tile_flag = c->fused_ctrl + 2 + 4 * nz;
-    F.plane_special = c->d_plane_special;
+    F.abort = c->fused_ctrl + 1;
+    F.tile_flag = c->fused_ctrl + 2;
+    F.tile_special = c->d_tile_special;
     F.timeout_ns = c->wait_limit_ns ? c->wait_limit_ns : kFusedTimeoutNs;
-    CUDA_TRY(c, cudaMemsetAsync(c->fused_ctrl, 0, sizeof(int) * (1 + 2 * (size_t)nz), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->fused_ctrl, 0, sizeof(int), c->stream));
     const int launched = c->model == LBM_MM ? mm_launch_fused2(aA, aB, F, c->stream) : hv_launch_fused2(aA, aB, F, c->stream);
     int rc = check_launch(c, launched);
     if (rc != LBM_OK) return rc;
@@ -350,7 +352,7 @@ int fused_pass(lbm_ctx* c) {
 int check_fused_abort(lbm_ctx* c) {
     if (!c->fused_pending || !c->fused_ctrl) return LBM_OK;
     int flag = 0;
-    int* abort = c->fused_ctrl + 1 + 2 * c->g.nz;
+    int* abort = c->fused_ctrl + 1;
     CUDA_TRY(c, cudaMemcpyAsync(&flag, abort, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->fused_pending = 0;
@@ -560,7 +562,7 @@ void release(lbm_ctx* c) {
     free_dev(c->fused_planes);
     c->fused_planes_bytes = 0;
     free_dev(c->fused_ctrl);
-    free_dev(c->d_plane_special);
+    free_dev(c->d_tile_special);
 }
 
 // Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
@@ -946,6 +948,7 @@ int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells) {
         if (ctx->stream) cudaStreamSynchronize(ctx->stream);
         else cudaDeviceSynchronize();
         free_dev(ctx->fused_ctrl);  // its flag array depends on the tile count
+        ctx->tile_special_version = -1;  // so do the tiles' source-cell offsets
         ctx->fused_tile = tile_cells;
     }
     ctx->fusion = mode;
@@ -1349,6 +1352,21 @@ int lbm_batch_step(lbm_batch* b, const int* steps) {
     int dev = -1;
     BCUDA_TRY(b, cudaGetDevice(&dev));
     if (dev != b->device) BCUDA_TRY(b, cudaSetDevice(b->device));
+    // A lattice whose planes fill the GPU runs its pairs of steps as two-step passes, launched as
+    // lbm_step launches them (the same kernels, so the same results bit for bit); the others
+    // advance together in the batched launches below. The passes are persistent launches over the
+    // whole GPU, so a graph would save nothing on them.
+    std::vector<int> batched(steps, steps + count);
+    for (int k = 0; k < count; ++k) {
+        lbm_ctx* c = b->ctx[k];
+        if (steps[k] < 2 || !fusion_eligible(c)) continue;
+        const int64_t before = c->launches;
+        const int rc = lbm_step(c, steps[k]);
+        if (rc != LBM_OK) return bfail(b, rc, "lbm_batch_step: context %d: %s", k, c->err.c_str());
+        b->launches += c->launches - before;
+        batched[(size_t)k] = 0;
+    }
+    steps = batched.data();
     const BatchPlan p = plan_batch(b, steps);
     if (p.max_steps == 0) return LBM_OK;
     int rc;
@@ -1539,13 +1557,13 @@ int longest_fitting(const lbm_ctx* c, int steps, size_t budget) {
 }
 
 // The checkpointed mode's segment length for `steps` steps: the longest whose work space stays
-// within that of ceil(sqrt(steps)) checkpoints and as many records, the classic sqrt(T) layout.
-// Its memory grows like sqrt(T); the longer final segment, recorded by the forward pass, spares
-// that many recomputed steps.
+// within that of segments of ceil(sqrt(steps)) steps (about sqrt(T) checkpoints and sqrt(T)
+// records, the classic layout). Its memory grows like sqrt(T); the longer final segment, recorded
+// by the forward pass, spares that many recomputed steps.
 int sqrt_interval(const lbm_ctx* c, int steps) {
-    const int k0 = std::max(1, (int)std::ceil(std::sqrt((double)steps)));
+    const int k0 = std::min(steps, std::max(1, (int)std::ceil(std::sqrt((double)steps))));
     Layout L;
-    const size_t classic = adjoint_layout(c, nullptr, k0, (steps + k0 - 1) / k0, 1, &L);
+    const size_t classic = adjoint_layout(c, nullptr, k0, earlier_segments(steps, k0), 1, &L);
     return std::max(k0, longest_fitting(c, steps, classic));
 }
 

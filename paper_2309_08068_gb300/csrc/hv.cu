@@ -276,15 +276,15 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
         }
     };
     fused_loop(F, aA.g.nx, nxy, nz, describe, [&](const FusedDesc& d) {
-        const int p = d.plane, j = d.j, base = p * nxy;
+        const int j = d.j, base = d.plane * nxy;
         if (d.type == kPhaseA) {
             const HVToRing<S> io{{stash}, static_cast<T4*>(d.ptr[0]), static_cast<T2*>(d.ptr[1]), base, nxy};
-            if (j < F.tiles) {
-                const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
-                for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
-                    hv_update<S, M, false, false>(aA, i, 0, io);
-            } else {
-                for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
+            const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
+            for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
+                hv_update<S, M, false, false>(aA, i, 0, io);
+            if (d.s_hi > d.s_lo) {  // the tile's source cells replace their ordinary update
+                named_sync(kComputeBarrier, kBlock);
+                for (int m = d.s_lo + threadIdx.x; m < d.s_hi; m += kBlock)
                     hv_update<S, M, true, false>(aA, aA.sv.cell[m], m, io);
             }
         } else {
@@ -294,12 +294,12 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
                                    {static_cast<const T2*>(d.ptr[3]), static_cast<const T2*>(d.ptr[4]),
                                     static_cast<const T2*>(d.ptr[5])},
                                    nxy};
-            if (j < F.tiles) {
-                const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
-                for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
-                    hv_update<S, M, false, false>(aB, i, 0, io);
-            } else {
-                for (int m = F.plane_special[p] + threadIdx.x; m < F.plane_special[p + 1]; m += kBlock)
+            const int end = min(base + (j + 1) * F.tile_cells, base + nxy);
+            for (int i = base + j * F.tile_cells + threadIdx.x; i < end; i += kBlock)
+                hv_update<S, M, false, false>(aB, i, 0, io);
+            if (d.s_hi > d.s_lo) {  // the tile's source cells replace their ordinary update
+                named_sync(kComputeBarrier, kBlock);
+                for (int m = d.s_lo + threadIdx.x; m < d.s_hi; m += kBlock)
                     hv_update<S, M, true, false>(aB, aB.sv.cell[m], m, io);
             }
         }

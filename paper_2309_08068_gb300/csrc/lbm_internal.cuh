@@ -513,14 +513,15 @@ __device__ __forceinline__ void add_plane_loss(const AdjointArgs& A, const Neigh
 // of both.
 // Phases run in the order A(nz-1), A(0), .., A(L-1), then B(k), A(k + L) for k = 0 .. nz-2-L,
 // then the remaining B phases (L >= 2: B(k) needs A(k + 1); R >= L + 1 keeps every wait on an
-// earlier item). A phase is `tiles` tiles of tile_cells consecutive cells of its plane, then one item for
-// the plane's source cells. Blocks take items in that order from a counter, and an item waits
-// only for items taken before it:
+// earlier item). A phase is `tiles` tiles of tile_cells consecutive cells of its plane. A tile
+// also recomputes the source cells among its own cells (after a barrier of its compute threads, so
+// that their values replace those of the ordinary update), so a finished tile is final, however
+// many source cells a plane holds. Blocks take tiles in that order from a counter, and a tile waits
+// only for tiles taken before it:
 //   * tile j of B(p) waits for the tiles of A(p - 1), A(p), A(p + 1) holding the rows next to its
-//     own (the cells it pulls from), and for those planes' source-cell items;
+//     own (the cells it pulls from);
 //   * tile j of A(p) waits for the same neighbourhood of tiles of the three B phases that read the
-//     slot's previous plane, p - R;
-//   * a source-cell item waits for every tile of its own phase.
+//     slot's previous plane, p - R.
 // Tiles publish the pass number in a flag of their own, so the flags need no reset between passes.
 // Every wait has a time limit; past it the pass sets `abort` and every block stops. A negative
 // limit makes every item that depends on another give up at its first check, met or not: the host
@@ -538,11 +539,9 @@ struct FusedArgs {
     int tiles;                  // tiles per plane
     int epoch;                  // this pass's number (>= 1); flags hold the last pass they finished
     int* next;                  // item counter (zero at launch)
-    int* count;                 // 2 nz finished-tile counters, A then B (zero at launch)
     int* tile_flag;             // 2 nz tiles flags, A then B
-    int* fix_flag;              // 2 nz source-cell item flags, A then B
     int* abort;                 // set when a wait timed out
-    const int* plane_special;   // nz + 1 offsets of each plane's cells in the special-cell list
+    const int* tile_special;    // nz tiles + 1 offsets of each tile's cells in the special-cell list
     long long timeout_ns;       // < 0: give up at the first dependency check
 };
 
@@ -633,20 +632,15 @@ __host__ __device__ __forceinline__ int fused_waits_on(int type, int plane, int 
     return 3;
 }
 
-__device__ __forceinline__ bool plane_has_sources(const FusedArgs& F, int p) {
-    return F.plane_special[p + 1] > F.plane_special[p];
-}
-
-// An item of a pass: phase (type, plane) and j < tiles for a tile, j == tiles for the plane's
-// source cells.
+// An item of a pass: tile j of phase (type, plane).
 struct FusedItem {
     int type, plane, j;
 };
 
-__device__ __forceinline__ FusedItem fused_item(int item, int per_phase, int nz, int L) {
+__device__ __forceinline__ FusedItem fused_item(int item, int tiles, int nz, int L) {
     FusedItem it;
-    const int q = item / per_phase;
-    it.j = item - q * per_phase;
+    const int q = item / tiles;
+    it.j = item - q * tiles;
     fused_phase(q, nz, L, &it.type, &it.plane);
     return it;
 }
@@ -661,20 +655,13 @@ __device__ inline bool fused_ready_warp(const FusedArgs& F, int nz, FusedItem it
     bool ok = true;
     // one look (wait == false) or a bounded wait
     auto reached = [&](const int* p, int target) { return wait ? fused_wait(F, p, target) : load_acquire(p) >= target; };
-    auto give_up = [&]() {  // negative limit: stop the pass at the first item with a dependency
-        if (lane == 0) atomicExch(F.abort, 1);
-        return false;
-    };
-    if (it.j == F.tiles) {  // source-cell item: every tile of its own phase
-        if (F.timeout_ns < 0) return give_up();
-        const bool own_tile = own.type == it.type && own.plane == it.plane && own.j < F.tiles;
-        if (lane == 0) ok = reached(F.count + it.type * nz + it.plane, F.tiles - (own_tile ? 1 : 0));
-        return __all_sync(0xffffffffu, ok);
-    }
     int q[3];
     int wtype = 0;
     if (fused_waits_on(it.type, it.plane, nz, F.R, &wtype, q) == 0) return true;
-    if (F.timeout_ns < 0) return give_up();
+    if (F.timeout_ns < 0) {  // negative limit: stop the pass at the first item with a dependency
+        if (lane == 0) atomicExch(F.abort, 1);
+        return false;
+    }
     int first, count;
     tile_window(it.j, F.tiles, F.tile_cells, nx, nxy, &first, &count);
     for (int idx = lane; ok && idx < 3 * count; idx += 32) {
@@ -684,21 +671,13 @@ __device__ inline bool fused_ready_warp(const FusedArgs& F, int nz, FusedItem it
         if (own.type == wtype && own.plane == q[k] && own.j == t) continue;
         ok = reached(F.tile_flag + ((size_t)wtype * nz + q[k]) * F.tiles + t, F.epoch);
     }
-    if (ok && lane < 3 && plane_has_sources(F, q[lane]) &&
-        !(own.type == wtype && own.plane == q[lane] && own.j == F.tiles))
-        ok = reached(F.fix_flag + wtype * nz + q[lane], F.epoch);
     return __all_sync(0xffffffffu, ok);
 }
 
-// Publish a finished item (after every store of the block: the caller's barrier orders them).
+// Publish a finished tile (after every store of the block: the caller's barrier orders them).
 __device__ __forceinline__ void fused_publish(const FusedArgs& F, int nz, FusedItem it) {
     __threadfence();
-    if (it.j < F.tiles) {
-        atomicExch(F.tile_flag + ((size_t)it.type * nz + it.plane) * F.tiles + it.j, F.epoch);
-        atomicAdd(F.count + it.type * nz + it.plane, 1);
-    } else {
-        atomicExch(F.fix_flag + it.type * nz + it.plane, F.epoch);
-    }
+    atomicExch(F.tile_flag + ((size_t)it.type * nz + it.plane) * F.tiles + it.j, F.epoch);
 }
 
 // Threads of a two-step block: kBlock compute threads and one scheduler warp.
@@ -753,15 +732,19 @@ __device__ __forceinline__ void named_arrive(int id, int count) {
 // it over in shared memory, so the compute threads do no index arithmetic per item.
 struct FusedDesc {
     int type, plane, j;
+    int s_lo, s_hi;  // the tile's source cells: entries s_lo .. s_hi - 1 of the special-cell list
     void* ptr[6];
 };
+
+// Barrier of a two-step block's compute threads alone (ids 1 and 2 are the hand-off barriers).
+constexpr int kComputeBarrier = 3;
 
 template <class Describe, class Work>
 __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, Describe&& describe, Work&& work) {
     constexpr int kHandoff = 1, kDone = 2;
     __shared__ int s_item[2], s_ok[2];
     __shared__ FusedDesc s_desc[2];
-    const int per_phase = F.tiles + 1;
+    const int per_phase = F.tiles;
     const int total = 2 * nz * per_phase;
     if (threadIdx.x < kBlock) {
         for (int buf = 0;; buf ^= 1) {
@@ -780,6 +763,9 @@ __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, D
         d.type = it.type;
         d.plane = it.plane;
         d.j = it.j;
+        const int* ts = F.tile_special + (size_t)it.plane * F.tiles + it.j;
+        d.s_lo = ts[0];
+        d.s_hi = ts[1];
         describe(it, d);
         return d;
     };

@@ -205,8 +205,9 @@ def test_adjoint_refuses_what_it_does_not_support(model):
 @pytest.mark.parametrize("model", ["mm", "hv"])
 def test_sqrt_interval_stays_within_the_classic_sqrt_layout(model):
     """The checkpointed mode's segment length is the longest whose work space does not exceed that
-    of ceil(sqrt(T)) checkpoints and as many records: at least ceil(sqrt(T)), a work space no larger
-    than the classic layout's, one step longer already over it, and the same result bit for bit."""
+    of segments of ceil(sqrt(T)) steps (the classic sqrt(T) layout): at least ceil(sqrt(T)), a work
+    space no larger than the classic layout's, one step longer already over it, and the same result
+    bit for bit."""
     from paper_2309_08068_gb300.lbm import lattice_from_workload
     w, f0, plane = small_case(model, seed=88)
     steps = 400  # long enough that keeping every record costs more than the classic layout

@@ -108,3 +108,41 @@ def test_refinement_sweep_full_size_batched_against_oracle(model):
         assert err <= 1e-5, (n, err)
         L.close()
     print(f"refinement sweep {model}: worst rel L2 {worst:.3e}")
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_batch_runs_wide_lattices_as_two_step_passes(model):
+    """Lattices whose planes fill the GPU run their pairs of steps as two-step passes inside the
+    batch, the others in the batched launches; with odd and even step counts, sources on full planes
+    and on columns, the result equals each lattice's own lbm_step bit for bit, twice in a row (the
+    second call replays the captured graph of the small lattices)."""
+    from paper_2309_08068_gb300.lbm import Batch, lattice_from_workload
+    stream = torch.cuda.Stream()
+    steps = [5, 6, 3, 7]
+
+    def lattices():
+        wide, f0 = wl.slab_case(model, (256, 160, 6), seed=160)
+        sweep = wl.skin_effect_3d(model, 208, 0.1)  # imposed plane wave on plane 0, 8 planes of it
+        sweep.shape = (208, 208, 8)
+        sweep.sigma = sweep.sigma[: 208 * 208 * 8].copy()
+        sweep.sigma[208 * 208 * 4:] = 0.1
+        small1, f2 = wl.random_state(model, (7, 5, 3), seed=161, media="few")
+        small2, f3 = wl.random_state(model, (33, 9, 4), seed=162, media="random")
+        out = []
+        for w, f in ((wide, f0), (sweep, None), (small1, f2), (small2, f3)):
+            L = lattice_from_workload(w, init=f is None, stream=stream)
+            if f is not None:
+                L.set_populations(np.asarray(f, np.float32) * 1e-2, 2)
+            out.append(L)
+        return out
+
+    solo, grouped = lattices(), lattices()
+    assert [L.step_fusion_active for L in grouped] == [True, True, False, False]
+    batch = Batch(grouped)
+    for rep in range(2):
+        for L, n in zip(solo, steps):
+            L.step(n)
+        batch.step(steps)
+        for k, (A, B) in enumerate(zip(solo, grouped)):
+            assert A.time == B.time
+            assert np.array_equal(A.populations_host(), B.populations_host()), (rep, k)

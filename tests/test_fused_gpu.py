@@ -187,3 +187,27 @@ def test_expired_wait_is_reported_by_host_reductions_and_reads():
         assert err.value.code == -5
     L.set_wait_limit(0)
     L.close()
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("tile", [256, 768])
+def test_fused_pairs_equal_single_steps_with_full_source_planes(model, tile):
+    """Every cell of a plane a source cell: an imposed plane wave on plane 0 (a wrap plane) and a
+    current over the whole of plane 3 and half of plane 4. Each tile recomputes its own source cells
+    after its ordinary update, so a plane of 40,960 source cells adds work to every tile of it
+    rather than to one item; the results must still equal single steps bit for bit."""
+    w, f = wl.random_state(model, PLANE + (7,), seed=150, media="few", n_sources=0)
+    nxy = PLANE[0] * PLANE[1]
+    rng = np.random.default_rng(151)
+    c = wl.LIGHT_SPEED[model]
+    w.sources = [
+        wl.Source("impose", np.arange(nxy, dtype=np.int64), wl.TimeFunction("sin", 1.0, 40.0, 0.3),
+                  E0=(1e-3, 0.0, 0.0), B0=(0.0, 1e-3 / c, 0.0)),
+        wl.Source("current", np.arange(3 * nxy, 4 * nxy + nxy // 2, dtype=np.int64),
+                  wl.TimeFunction("sin", 1e-3, 17.0, 0.1), w=rng.standard_normal((nxy + nxy // 2, 3))),
+    ]
+    q = 48 if model == "mm" else 36
+    active, fused = run(w, f, 5, 2, tile)
+    assert active
+    _, single = run(w, f, 5, 0)
+    assert_same(fused, single, q)

@@ -156,3 +156,17 @@ def test_slab_arguments_are_checked():
     assert G.lib.lbm_halo_pack(G.h, 2, G.halo_pack(0).data_ptr(), 1) != 0
     L.close()
     G.close()
+
+
+def test_bench_slab_split_runs_on_one_rank():
+    """The benchmark's z-slab mode (bench.time_slab_split) on one rank: the single slab closes the
+    periodic ring on itself, so every step packs and unpacks both faces through the same exchange
+    schedule the multi-rank run uses, and the fields stay finite."""
+    import bench
+    stream = torch.cuda.Stream()
+    res = bench.time_slab_split(64, 16, 4, 3, 0, 1, stream)
+    assert res["finite"]
+    assert res["slab_planes"] == (0, 16)
+    assert res["launches"] > 0 and res["elapsed_ms"] > 0 and res["e2e_s"] > 0
+    assert res["halo_bytes_sent_per_step"]["mm"] == 2 * 4 * 16 * 64 * 64
+    assert res["halo_bytes_sent_per_step"]["hv"] == 2 * (16 + 8) * 64 * 64
