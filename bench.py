@@ -292,9 +292,9 @@ def refinement_sweep(stream, steps: int):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_own = e0.elapsed_time(e1)
-        passes = [L.step_fusion_active for L in lats]
+        passes = [L.pass_kind for L in lats]
         out[model] = {"lattices": len(works), "cells": cells, "steps": steps,
-                      "lattices_with_two_step_pass": [w.shape[0] for w, a in zip(works, passes) if a],
+                      "two_step_pass_by_size": {str(w.shape[0]): a for w, a in zip(works, passes) if a},
                       "batched_graph_MLUPS": round(cells * steps / (ms_batched * 1e-3) / 1e6, 1),
                       "per_lattice_launches_MLUPS": round(cells * steps / (ms_single * 1e-3) / 1e6, 1),
                       "per_lattice_lbm_step_MLUPS": round(cells * steps / (ms_own * 1e-3) / 1e6, 1),
@@ -489,7 +489,8 @@ def run_ours(args):
             lats[model] = lattice_from_workload(w, stream=stream, storage=args.storage, storage_scale=scale)
             lats[model].set_step_fusion(args.fusion)
     torch.cuda.synchronize()
-    fused = {m: L.step_fusion_active for m, L in lats.items()}
+    kinds = {m: L.pass_kind for m, L in lats.items()}  # "tiled", "ring" or None (single steps)
+    fused = {m: k is not None for m, k in kinds.items()}
 
     def chunks(k):
         """Steps per call: pairs when lbm_step runs two steps per pass, singles otherwise."""
@@ -530,18 +531,23 @@ def run_ours(args):
     for L in lats.values():
         L.sync()  # also reports a pass whose dependency wait timed out
 
-    # the same lattices one step per launch (the single-step kernels), for reference
-    single = {}
+    # the same lattices one step per launch (the single-step kernels), and as ring passes (the
+    # wavefront with its intermediate planes in L2), for reference
+    single, ring = {}, {}
     for model, L in lats.items():
-        L.set_step_fusion(0)
         k1 = max(10, min(args.steps, 50))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        L.step(k1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        single[model] = e0.elapsed_time(e1) / k1
+        for mode, out, per_call in ((0, single, 1), (2, ring, 2)):
+            L.set_step_fusion(mode)
+            if mode == 2 and L.pass_kind != "ring":
+                continue
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(k1 // per_call):
+                L.step(per_call)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[model] = e0.elapsed_time(e1) / (k1 // per_call * per_call)
         L.set_step_fusion(args.fusion)
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     finite = all(L.check_finite() for L in lats.values())
@@ -567,8 +573,8 @@ def run_ours(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / kv
-            fv = Lv.step_fusion_active
-            nbytes = BYTES_PER_CELL[model] // 2 // (2 if fv else 1)  # per cell and step
+            fv = Lv.pass_kind
+            nbytes = BYTES_PER_CELL[model] // 2 // (2 if fv is not None else 1)  # per cell and step
             variants[st][model] = {"MLUPS": round(ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
                                    "two_steps_per_pass": fv, "bytes_per_cell_step": nbytes,
                                    "algorithmic_GBps": round(nbytes * ncell / (ms * 1e-3) / 1e9, 1),
@@ -613,7 +619,8 @@ def run_ours(args):
     bpc = {m: bpc1[m] // (2 if fused[m] else 1) for m in bpc1}
     mm_gbs = bpc["mm"] * ncell / (mm_ms * 1e-3) / 1e9
     hv_gbs = bpc["hv"] * ncell / (hv_ms * 1e-3) / 1e9
-    kname = {m: (f"{m}_fused2_kernel" if fused[m] else f"{m}_step_kernel") for m in fused}
+    kname = {m: {"tiled": f"{m}_tile2_kernel", "ring": f"{m}_fused2_kernel", None: f"{m}_step_kernel"}[kinds[m]]
+             for m in kinds}
     # ncu traffic is per launch: a fused launch covers two steps
     traffic = ncu_traffic(kname["mm"], ncell) if args.storage == "f32" else None
     hv_traffic = ncu_traffic(kname["hv"], ncell) if args.storage == "f32" else None
@@ -621,10 +628,10 @@ def run_ours(args):
     l2 = l2_resident_bandwidth(stream)
     # Second roofline, against L2 writes (stores from the SMs plus fills from HBM). Per cell, a
     # single step writes its populations into L2 twice (the output, and the fill of its inputs from
-    # HBM); a two-step pass writes them three times per two steps (the ring slot, the output and
-    # the fill), 1.5 times per step. Every kernel here runs at about the L2-resident write rate.
+    # HBM); a ring pass three times per two steps (the ring slot, the output and the fill), 1.5 times
+    # per step; a tiled pass twice per two steps (the fill and the output), once per step.
     pop = {m: bpc1[m] // 2 for m in bpc1}
-    l2w = {m: (3 * pop[m] // 2 if fused[m] else 2 * pop[m]) for m in pop}
+    l2w = {m: {"tiled": pop[m], "ring": 3 * pop[m] // 2, None: 2 * pop[m]}[kinds[m]] for m in pop}
     step_ms = {"mm": mm_ms, "hv": hv_ms}
     l2_roof = {m: {"kernel": kname[m], "bytes_per_cell_step": l2w[m],
                    "achieved": round(l2w[m] * ncell / (step_ms[m] * 1e-3) / 1e9, 1), "peak": l2["write_GBps"],
@@ -650,12 +657,15 @@ def run_ours(args):
                    "parallelism": f"independent lattices per rank x{world}"},
         "per_model": {
             "mm": {"MLUPS": round(ncell / (mm_ms * 1e-3) / 1e6, 2), "ms_per_step": round(mm_ms, 4),
-                   "two_steps_per_pass": fused["mm"], "kernel": kname["mm"],
+                   "two_steps_per_pass": kinds["mm"], "kernel": kname["mm"],
                    "algorithmic_GBps": round(mm_gbs, 1), "bytes_per_cell_step": bpc["mm"]},
             "hv": {"MLUPS": round(ncell / (hv_ms * 1e-3) / 1e6, 2), "ms_per_step": round(hv_ms, 4),
-                   "two_steps_per_pass": fused["hv"], "kernel": kname["hv"],
+                   "two_steps_per_pass": kinds["hv"], "kernel": kname["hv"],
                    "algorithmic_GBps": round(hv_gbs, 1), "bytes_per_cell_step": bpc["hv"]},
         },
+        "ring_pass": {
+            m: {"kernel": f"{m}_fused2_kernel", "ms_per_step": round(ring[m], 4),
+                "MLUPS": round(ncell / (ring[m] * 1e-3) / 1e6, 2)} for m in ring},
         "single_step_kernels": {
             m: {"ms_per_step": round(single[m], 4), "MLUPS": round(ncell / (single[m] * 1e-3) / 1e6, 2),
                 "bytes_per_cell_step": bpc1[m], "algorithmic_GBps": round(single_gbs[m], 1),

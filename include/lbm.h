@@ -214,17 +214,22 @@ int lbm_sync(lbm_ctx* ctx);
 int lbm_destroy(lbm_ctx* ctx);
 
 /* Two time steps per pass. A step reads only a cell's 3 x 3 x 3 neighbourhood (advection, Sections
- * II and III), so lbm_step(ctx, n >= 2) can run steps t and t + 1 as one wavefront along z: one
- * persistent launch updates plane p at step t into a small ring of intermediate planes, and plane
- * p at step t + 1 once planes p - 1, p, p + 1 of step t exist. The ring is meant to stay in L2, so
- * each pair of steps reads and writes the populations in HBM once instead of twice. The results
- * equal single steps bit for bit (same arithmetic; the intermediate planes hold the populations in
- * the context's storage format).
- *   mode 0: never; 1 (default): with FP32 storage, when the intermediate planes (R + 2 planes of
- *   populations: R = 5 for MM, 6 for HV) fit in three quarters of L2 and a plane has at least 256
- *   cells per SM (with 16-bit storage the single-step kernels are faster on GB300);
- *   2: whenever a plane has that many cells.
- * Never for z_ghost slabs or track_rho contexts, nor with nz < 4 (MM) or 5 (HV). The pass's dependency waits are
+ * II and III), so lbm_step(ctx, n >= 2) can run steps t and t + 1 in one launch, reading and writing
+ * the populations in HBM once per pair of steps instead of twice. Two such passes exist, and both
+ * equal single steps bit for bit (same arithmetic; the intermediate step is held in the context's
+ * storage format):
+ *   the tiled pass: each block steps a 14 x 14 tile of a chunk of planes plus a ring of one cell
+ *   around it (16 x 16 cells, one thread each) twice, keeping the intermediate step in shared
+ *   memory as it marches along z; blocks never wait for one another. Needs nx, ny >= 16, nz >= 3.
+ *   the ring pass: one persistent launch runs the two steps as a wavefront along z, updating plane
+ *   p at step t into a ring of intermediate planes meant to stay in L2, and plane p at step t + 1
+ *   once planes p - 1, p, p + 1 of step t exist. Needs a plane of at least 256 cells per SM and
+ *   nz >= 4 (MM) or 5 (HV).
+ *   mode 0: never; 1 (default): with FP32 storage, the pass measured fastest on GB300: for MM the
+ *   tiled pass where it applies, for HV the ring pass when its intermediate planes (R + 2 planes:
+ *   R = 5 for MM, 6 for HV) fit in three quarters of L2; 2: the ring pass wherever it applies;
+ *   3: the tiled pass wherever it applies (any storage).
+ * Never for z_ghost slabs or track_rho contexts. The ring pass's dependency waits are
  * bounded (2 s, lbm_set_wait_limit); if one expires every block of the pass stops, the populations
  * of that pass are undefined, and the next lbm_sync, lbm_reduce, lbm_reduce_noalloc or host-side
  * lbm_fields / lbm_get_populations returns LBM_ETIMEDOUT (once; until then later passes stop
@@ -240,7 +245,8 @@ int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells);
  * deterministically: the pass stops and the next waiting call returns LBM_ETIMEDOUT. Takes effect
  * from the next pass. */
 int lbm_set_wait_limit(lbm_ctx* ctx, long long ns);
-/* 1 when lbm_step would run pairs of steps as single passes, 0 when not (negative on error). */
+/* How lbm_step would run pairs of steps: 0 as single steps, 1 as ring passes, 2 as tiled passes
+ * (negative on error). */
 int lbm_step_fusion_active(lbm_ctx* ctx);
 /* Self-check of the two-step pass's work order on the host, with the kernel's own order and tile
  * window functions, for an nx x ny x nz lattice, ring R, lookahead L and tile_cells per item
@@ -252,6 +258,15 @@ int lbm_step_fusion_active(lbm_ctx* ctx);
  * Returns 0 when all hold, the number of the first failed check otherwise, LBM_EINVAL for bad
  * sizes. Needs no GPU. */
 int lbm_fused_schedule_check(int nx, int ny, int nz, int R, int L, int tile_cells);
+/* Self-check of the tiled pass's geometry on the host, with the kernel's own tile functions, for an
+ * nx x ny plane (nx, ny >= 16, nx * ny <= 2^22). Checks:
+ *   1. the 16 x 16 positions of an extended tile are distinct cells;
+ *   2. the 3 x 3 neighbours of a tile's own cell lie in its extended tile and are the cell's lattice
+ *      neighbours (periodic);
+ *   3. the tiles' own cells cover the plane exactly once.
+ * Returns 0 when all hold, the number of the first failed check otherwise, LBM_EINVAL for bad
+ * sizes. Needs no GPU. */
+int lbm_tiled_layout_check(int nx, int ny);
 
 /* Loss and gradient over the next `steps` time steps (inverse material design; the paper itself
  * only runs forward). From the current populations, the context advances `steps` steps exactly as

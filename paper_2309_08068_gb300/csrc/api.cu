@@ -78,13 +78,16 @@ struct lbm_ctx {
     void* halo_stage = nullptr;
     size_t halo_stage_bytes = 0;
     // two steps per pass (lbm_step with n >= 2): mode, intermediate planes, counters
-    int fusion = 1;                // 0 off, 1 when the ring fits the L2 budget, 2 whenever possible
+    int fusion = 1;                // 0 off, 1 automatic, 2 the L2-ring pass, 3 the tiled pass, when possible
     int fused_tile = 0;            // cells per work item of a pass (0: the model's default)
     void* fused_planes = nullptr;  // R ring slots + the slots of planes 0 and nz - 1
     size_t fused_planes_bytes = 0;
     int* fused_ctrl = nullptr;     // item counter, abort, 2 nz tiles tile flags
     int fused_epoch = 0;           // number of the last pass launched
     int* d_tile_special = nullptr;  // nz tiles + 1 offsets of each tile's cells in the special-cell list
+    int* d_tiled_off = nullptr;     // tiled pass: tiles nz + 1 offsets into d_tiled_entries, by (tile, plane)
+    int2* d_tiled_entries = nullptr;  // tiled pass: (special-cell index, extended-tile position)
+    int tiled_version = -1;           // sources_version the two arrays were built for
     int tile_special_version = -1;   // sources_version it was built for (-1: rebuild)
     int sources_version = 0;
     int fused_pending = 0;         // a pass ran since the abort flag was last read
@@ -235,11 +238,13 @@ size_t fused_plane_bytes(const lbm_ctx* c) {
     return (group_bytes(c->model, c->storage) + (c->model == LBM_HV ? pair_bytes(c->storage) : 0)) * nxy;
 }
 
-// Pairs of steps run as one pass when the wavefront has enough tiles per plane to fill the GPU and
-// (mode 1) the populations are stored in FP32 and the intermediate planes fit in three quarters
-// of L2, where they are meant to stay.
-bool fusion_eligible(const lbm_ctx* c) {
-    if (c->fusion == 0 || c->z_ghost || c->track_rho || c->g.nz < std::max(3, fused_shape(c).L + 1)) return false;
+// The L2-ring pass applies when the wavefront has enough tiles per plane to fill the GPU and, by
+// default, the populations are stored in FP32 and the intermediate planes fit in three quarters of
+// L2, where they are meant to stay.
+bool ring_eligible(const lbm_ctx* c) {
+    if (c->fusion == 0 || c->fusion == 3 || c->z_ghost || c->track_rho ||
+        c->g.nz < std::max(3, fused_shape(c).L + 1))
+        return false;
     int dev = 0, sms = 0, l2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -254,6 +259,26 @@ bool fusion_eligible(const lbm_ctx* c) {
     // per step against 0.62, HV 0.36 against 0.49).
     if (c->fusion == 1 && c->storage != LBM_F32) return false;
     return true;
+}
+
+// The tiled pass needs a whole extended tile of distinct cells in x and y.
+bool tiled_possible(const lbm_ctx* c) {
+    return !c->z_ghost && !c->track_rho && c->g.nz >= 3 && c->g.nx >= kTileEX && c->g.ny >= kTileEY;
+}
+
+enum { kPassNone = 0, kPassRing = 1, kPassTiled = 2 };
+
+// Which two-step pass lbm_step(n >= 2) runs: mode 2 the ring, mode 3 the tiles, wherever each is
+// possible. Mode 1 takes what measured fastest on GB300 with FP32 storage: for MM the tiled pass
+// (256^3 dipole: 0.710 ms per step against 0.745 for the ring pass and 0.932 for single steps;
+// 128^3: 0.122 against 0.130 for single steps), for HV the ring pass where it applies, else single
+// steps (the tiled HV pass is held by shared-memory instruction throughput: 0.682 ms per step at
+// 256^3 against 0.516 for the ring pass, and slower than single steps at 128^3).
+int pass_kind(const lbm_ctx* c) {
+    if (c->fusion == 0) return kPassNone;
+    if (c->fusion == 3) return tiled_possible(c) ? kPassTiled : kPassNone;
+    if (c->fusion == 1 && c->model == LBM_MM && c->storage == LBM_F32 && tiled_possible(c)) return kPassTiled;
+    return ring_eligible(c) ? kPassRing : kPassNone;
 }
 
 int ensure_fused(lbm_ctx* c) {
@@ -291,6 +316,8 @@ int ensure_fused(lbm_ctx* c) {
             off[k] = (int)m;
         }
         free_dev(c->d_tile_special);
+    free_dev(c->d_tiled_off);
+    free_dev(c->d_tiled_entries);
         if (cudaMalloc(&c->d_tile_special, sizeof(int) * off.size()) != cudaSuccess) {
             cudaGetLastError();
             c->d_tile_special = nullptr;
@@ -304,7 +331,6 @@ int ensure_fused(lbm_ctx* c) {
 
 int fused_pass(lbm_ctx* c) {
     const int in = c->cur, out = 1 - c->cur;
-    const int nz = c->g.nz;
     StepArgs aA = base_args(c), aB = base_args(c);
     bind_buffers(c, aA, in, out);
     bind_buffers(c, aB, in, out);
@@ -362,6 +388,93 @@ int check_fused_abort(lbm_ctx* c) {
                     "a two-step pass stopped: a dependency wait exceeded its time limit; the populations "
                     "of that pass are undefined (restore them with lbm_set_populations)");
     }
+    return LBM_OK;
+}
+
+// --- two steps per pass over shared-memory tiles ----------------------------------------------
+int tiled_tiles_x(const lbm_ctx* c) { return (c->g.nx + kTileTX - 1) / kTileTX; }
+int tiled_tiles_y(const lbm_ctx* c) { return (c->g.ny + kTileTY - 1) / kTileTY; }
+
+// The source cells of every tile's extended cells, by (tile, plane): the tiled pass recomputes them
+// after each ordinary update of their plane.
+int ensure_tiled(lbm_ctx* c) {
+    if (c->tiled_version == c->sources_version && c->d_tiled_off) return LBM_OK;
+    const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz, nxy = nx * ny;
+    const int tx = tiled_tiles_x(c), ty = tiled_tiles_y(c);
+    // extended positions (tile, position) at which each lattice x, and each y, appears
+    std::vector<std::vector<std::pair<int, int>>> xs((size_t)nx), ys((size_t)ny);
+    for (int b = 0; b < tx; ++b)
+        for (int e = 0; e < kTileEX; ++e) xs[(size_t)tile_coord(b, e, kTileTX, nx)].emplace_back(b, e);
+    for (int b = 0; b < ty; ++b)
+        for (int e = 0; e < kTileEY; ++e) ys[(size_t)tile_coord(b, e, kTileTY, ny)].emplace_back(b, e);
+    struct Entry {
+        long long key;  // tile nz + plane
+        int m, local;
+    };
+    std::vector<Entry> entries;
+    for (size_t m = 0; m < c->h_cell.size(); ++m) {
+        const int cell = c->h_cell[m], z = cell / nxy, r = cell - z * nxy, y = r / nx, x = r - y * nx;
+        for (const auto& px : xs[(size_t)x])
+            for (const auto& py : ys[(size_t)y])
+                entries.push_back(Entry{(long long)(px.first + tx * py.first) * nz + z, (int)m,
+                                        px.second + kTileEX * py.second});
+    }
+    std::stable_sort(entries.begin(), entries.end(), [](const Entry& a, const Entry& b) { return a.key < b.key; });
+    const size_t keys = (size_t)tx * ty * nz;
+    std::vector<int> off(keys + 1, 0);
+    std::vector<int2> list(std::max<size_t>(entries.size(), 1));
+    for (size_t k = 0; k < entries.size(); ++k) {
+        off[(size_t)entries[k].key + 1] += 1;
+        list[k] = make_int2(entries[k].m, entries[k].local);
+    }
+    for (size_t k = 0; k < keys; ++k) off[k + 1] += off[k];
+    free_dev(c->d_tiled_off);
+    free_dev(c->d_tiled_entries);
+    if (cudaMalloc(&c->d_tiled_off, sizeof(int) * off.size()) != cudaSuccess ||
+        cudaMalloc(&c->d_tiled_entries, sizeof(int2) * list.size()) != cudaSuccess) {
+        cudaGetLastError();
+        free_dev(c->d_tiled_off);
+        free_dev(c->d_tiled_entries);
+        return fail(c, LBM_ENOMEM, "lbm_step: cannot allocate the tiles' source-cell lists");
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_tiled_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_tiled_entries, list.data(), sizeof(int2) * list.size(), cudaMemcpyHostToDevice));
+    c->tiled_version = c->sources_version;
+    return LBM_OK;
+}
+
+// Planes per block: enough blocks for about four waves of the resident ones (each chunk steps two
+// extra planes of the extended tile), and at least 8 planes.
+int tiled_chunk(const lbm_ctx* c) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        cudaGetLastError();
+    const int occ = std::max(1, c->model == LBM_MM ? mm_tile2_occupancy(c->storage, c->media_mode)
+                                                   : hv_tile2_occupancy(c->storage, c->media_mode));
+    const long long tiles = (long long)tiled_tiles_x(c) * tiled_tiles_y(c);
+    const long long want = (4LL * sms * occ + tiles - 1) / tiles;  // chunks per tile column
+    const int chunk = (int)((c->g.nz + want - 1) / want);
+    return std::min(c->g.nz, std::max(8, chunk));
+}
+
+int tiled_pass(lbm_ctx* c) {
+    const int in = c->cur, out = 1 - c->cur;
+    StepArgs aA = base_args(c), aB = base_args(c);
+    bind_buffers(c, aA, in, out);
+    bind_buffers(c, aB, in, out);
+    fill_scalars(c, aA, c->t + 1);
+    fill_scalars(c, aB, c->t + 2);
+    TileArgs T;
+    T.tiles_x = tiled_tiles_x(c);
+    T.tiles_y = tiled_tiles_y(c);
+    T.chunk = tiled_chunk(c);
+    T.entry_off = c->d_tiled_off;
+    T.entries = c->d_tiled_entries;
+    const int launched = c->model == LBM_MM ? mm_launch_tile2(aA, aB, T, c->stream) : hv_launch_tile2(aA, aB, T, c->stream);
+    int rc = check_launch(c, launched);
+    if (rc != LBM_OK) return rc;
+    c->cur = out;
+    c->t += 2;
     return LBM_OK;
 }
 
@@ -563,6 +676,8 @@ void release(lbm_ctx* c) {
     c->fused_planes_bytes = 0;
     free_dev(c->fused_ctrl);
     free_dev(c->d_tile_special);
+    free_dev(c->d_tiled_off);
+    free_dev(c->d_tiled_entries);
 }
 
 // Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
@@ -790,10 +905,15 @@ int lbm_step(lbm_ctx* ctx, int n) {
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
     int s = 0;
-    if (n >= 2 && fusion_eligible(ctx)) {
+    const int kind = n >= 2 ? pass_kind(ctx) : kPassNone;
+    if (kind == kPassRing) {
         if ((rc = ensure_fused(ctx)) != LBM_OK) return rc;
         for (; s + 2 <= n; s += 2)
             if ((rc = fused_pass(ctx)) != LBM_OK) return rc;
+    } else if (kind == kPassTiled) {
+        if ((rc = ensure_tiled(ctx)) != LBM_OK) return rc;
+        for (; s + 2 <= n; s += 2)
+            if ((rc = tiled_pass(ctx)) != LBM_OK) return rc;
     }
     StepArgs a = base_args(ctx);
     for (; s < n; ++s) {
@@ -940,7 +1060,7 @@ int lbm_sync(lbm_ctx* ctx) {
 
 int lbm_set_step_fusion(lbm_ctx* ctx, int mode, int tile_cells) {
     if (!ctx) return LBM_EINVAL;
-    if (mode < 0 || mode > 2) return fail(ctx, LBM_EINVAL, "lbm_set_step_fusion: mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(ctx, LBM_EINVAL, "lbm_set_step_fusion: mode must be 0, 1, 2 or 3");
     if (tile_cells < 0 || tile_cells % kBlock != 0 || tile_cells > 16 * kBlock)
         return fail(ctx, LBM_EINVAL, "lbm_set_step_fusion: tile_cells must be 0 or a multiple of %d up to %d", kBlock,
                     16 * kBlock);
@@ -965,7 +1085,7 @@ int lbm_step_fusion_active(lbm_ctx* ctx) {
     if (!ctx) return LBM_EINVAL;
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
-    return fusion_eligible(ctx) ? 1 : 0;
+    return pass_kind(ctx);
 }
 
 }  // extern "C"
@@ -1359,7 +1479,7 @@ int lbm_batch_step(lbm_batch* b, const int* steps) {
     std::vector<int> batched(steps, steps + count);
     for (int k = 0; k < count; ++k) {
         lbm_ctx* c = b->ctx[k];
-        if (steps[k] < 2 || !fusion_eligible(c)) continue;
+        if (steps[k] < 2 || pass_kind(c) == kPassNone) continue;
         const int64_t before = c->launches;
         const int rc = lbm_step(c, steps[k]);
         if (rc != LBM_OK) return bfail(b, rc, "lbm_batch_step: context %d: %s", k, c->err.c_str());
@@ -1912,6 +2032,42 @@ extern "C" int lbm_halo_exchange(lbm_ctx* lower, lbm_ctx* upper) {
     for (int k = 0; k < down_src.count; ++k)
         h.c[h.count++] = HaloChunk{down_src.ptr[k], down_dst.ptr[k], (long long)down_src.bytes[k]};
     return check_launch(lower, launch_halo_copy(h, lower->stream));
+}
+
+// ------------------------------------------------------------------------------------------------
+// lbm_tiled_layout_check: the tiled pass's geometry, checked on the host with the kernel's own
+// tile_coord and tile_core.
+// ------------------------------------------------------------------------------------------------
+extern "C" int lbm_tiled_layout_check(int nx, int ny) {
+    if (nx < kTileEX || ny < kTileEY || (long long)nx * ny > (1 << 22)) return LBM_EINVAL;
+    const int tx = (nx + kTileTX - 1) / kTileTX, ty = (ny + kTileTY - 1) / kTileTY;
+    std::vector<int> owner((size_t)nx * ny, 0);
+    for (int by = 0; by < ty; ++by)
+        for (int bx = 0; bx < tx; ++bx) {
+            std::vector<char> seen((size_t)nx * ny, 0);
+            for (int local = 0; local < kTileThreads; ++local) {
+                const int ex = local % kTileEX, ey = local / kTileEX;
+                const int x = tile_coord(bx, ex, kTileTX, nx), y = tile_coord(by, ey, kTileTY, ny);
+                // 1. an extended tile's positions are distinct cells
+                if (seen[(size_t)x + (size_t)nx * y]++) return 1;
+                if (!tile_core(local, bx, by, nx, ny)) continue;
+                owner[(size_t)x + (size_t)nx * y] += 1;
+                // 2. a core position's neighbours lie in the extended tile and are the lattice
+                //    neighbours (periodic)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int nex = ex + dx, ney = ey + dy;
+                        if (nex < 0 || nex >= kTileEX || ney < 0 || ney >= kTileEY) return 2;
+                        if (tile_coord(bx, nex, kTileTX, nx) != (x + dx + nx) % nx ||
+                            tile_coord(by, ney, kTileTY, ny) != (y + dy + ny) % ny)
+                            return 3;
+                    }
+            }
+        }
+    // 3. the cores cover every cell exactly once
+    for (int k : owner)
+        if (k != 1) return 4;
+    return LBM_OK;
 }
 
 // ------------------------------------------------------------------------------------------------

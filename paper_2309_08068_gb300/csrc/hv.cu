@@ -306,6 +306,122 @@ __global__ void __launch_bounds__(kFusedThreads, 3) hv_fused2_kernel(StepArgs aA
     });
 }
 
+// Two steps per pass over shared-memory tiles (see TileArgs). Directions by v_z: class 0 (v1 .. v4,
+// in-plane), class 1 (v6 = +z), class 2 (v5 = -z).
+__host__ __device__ constexpr int hv_zclass(int k) { return k < 4 ? 0 : (k == 5 ? 1 : 2); }
+__host__ __device__ constexpr int hv_zrank(int k) { return k < 4 ? k : 0; }
+
+// Direction planes of kTileThreads cells, for the 4-vectors and again for the 2-vectors: plane 0
+// holds class 2 of the newest plane, 1-4 and 5-8 class 0 of the last two planes, 9-11 class 1 of
+// the last three.
+template <int S>
+struct HVTile {
+    using T4 = typename Pack4<S>::T;
+    using T2 = typename Pack2<S>::T;
+    static constexpr size_t kBytes = 12 * kTileThreads * (sizeof(T4) + sizeof(T2));
+    T4* base4;
+    T2* base2;
+    __device__ int slot(int cls, int p) const {  // first direction plane of the class's slot, plane p >= -1
+        return cls == 2 ? 0 : (cls == 0 ? 1 + 4 * ((p + 3) % 2) : 9 + (p + 3) % 3);
+    }
+};
+
+template <int S>
+struct HVToTile : NoStash {
+    using T4 = typename Pack4<S>::T;
+    using T2 = typename Pack2<S>::T;
+    T4* base4;
+    T2* base2;
+    int slot[3];  // by class, for plane p
+    int local;
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) const {
+        hv_pull<S>(a, h, e, hy);
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int k, int, float4 ev, float2 hv) const {
+        const int at = (slot[hv_zclass(k)] + hv_zrank(k)) * kTileThreads + local;
+        base4[at] = Pack4<S>::pack(ev, a.scale);
+        base2[at] = Pack2<S>::pack(hv, a.scale);
+    }
+};
+
+template <int S>
+struct HVFromTile : NoStash {
+    using T4 = typename Pack4<S>::T;
+    using T2 = typename Pack2<S>::T;
+    const T4* base4;
+    const T2* base2;
+    int slot[3];  // class 0 of plane q, class 1 of q - 1, class 2 of q + 1
+    int local;
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood&, float4 (&e)[6], float2 (&hy)[6]) const {
+        static_for<0, 6>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int ax = kHVAxis[k], sg = kHVSign[k];
+            constexpr int vx = ax == 0 ? sg : 0, vy = ax == 1 ? sg : 0;
+            const int at = (slot[hv_zclass(k)] + hv_zrank(k)) * kTileThreads + local - (vx + vy * kTileEX);
+            e[k] = Pack4<S>::unpack(base4[at], a.inv_scale);
+            hy[k] = Pack2<S>::unpack(base2[at], a.inv_scale);
+        });
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int k, int i, float4 ev, float2 hv) const {
+        T4* __restrict__ eout = static_cast<T4*>(a.fout);
+        T2* __restrict__ hout = static_cast<T2*>(a.fout2);
+        __stcs(eout + (size_t)k * a.g.n + i, Pack4<S>::pack(ev, a.scale));
+        __stcs(hout + (size_t)k * a.g.n + i, Pack2<S>::pack(hv, a.scale));
+    }
+};
+
+template <int S, int M>
+__global__ void __launch_bounds__(kTileThreads, S == kF32 ? 3 : 4) hv_tile2_kernel(StepArgs aA, StepArgs aB,
+                                                                                    TileArgs T) {
+    using T4 = typename Pack4<S>::T;
+    using T2 = typename Pack2<S>::T;
+    extern __shared__ __align__(16) unsigned char hv_tile_smem[];
+    const HVTile<S> tile{reinterpret_cast<T4*>(hv_tile_smem),
+                         reinterpret_cast<T2*>(hv_tile_smem + 12 * kTileThreads * sizeof(T4))};
+    const int nz = aA.g.nz, nxy = aA.g.nx * aA.g.ny;
+    const TileCell c = tile_cell(aA.g, T);
+    const int* off = T.entry_off + (size_t)c.tile * nz;
+    for (int p = c.z0 - 1; p <= c.z1; ++p) {
+        const int pz = tile_wrap(p, nz);
+        {  // phase A: step t of the extended tile's cells of plane pz
+            const HVToTile<S> io{{}, tile.base4, tile.base2, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)},
+                                 (int)threadIdx.x};
+            hv_update<S, M, false, false>(aA, pz * nxy + c.cxy, 0, io);
+            const int lo = off[pz], hi = off[pz + 1];
+            if (hi > lo) {  // the source cells among them replace their ordinary update
+                __syncthreads();
+                for (int k = lo + threadIdx.x; k < hi; k += kTileThreads) {
+                    const int2 e = T.entries[k];
+                    const HVToTile<S> sio{{}, io.base4, io.base2, {io.slot[0], io.slot[1], io.slot[2]}, e.y};
+                    hv_update<S, M, true, false>(aA, aA.sv.cell[e.x], e.x, sio);
+                }
+            }
+        }
+        __syncthreads();
+        if (p > c.z0) {  // phase B: step t + 1 of the tile's own cells of plane q = p - 1
+            const int q = p - 1;
+            const HVFromTile<S> io{{}, tile.base4, tile.base2, {tile.slot(0, q), tile.slot(1, q - 1), tile.slot(2, q + 1)},
+                                   (int)threadIdx.x};
+            if (c.core) hv_update<S, M, false, false>(aB, q * nxy + c.cxy, 0, io);
+            const int lo = off[q], hi = off[q + 1];
+            if (hi > lo) {
+                __syncthreads();
+                for (int k = lo + threadIdx.x; k < hi; k += kTileThreads) {
+                    const int2 e = T.entries[k];
+                    if (!tile_core(e.y, c.bx, c.by, aA.g.nx, aA.g.ny)) continue;
+                    const HVFromTile<S> sio{{}, io.base4, io.base2, {io.slot[0], io.slot[1], io.slot[2]}, e.y};
+                    hv_update<S, M, true, false>(aB, aB.sv.cell[e.x], e.x, sio);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <int S, int M, bool kSpecial>
 __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
     if constexpr (kSpecial) {
@@ -757,6 +873,40 @@ int hv_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F,
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             hv_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
+        });
+    });
+    return 1;
+}
+
+template <int S, int M>
+void hv_tile2_prepare() {
+    static bool done = false;  // the attribute is a property of the kernel: set it once per process
+    if (!done) {
+        cudaFuncSetAttribute(hv_tile2_kernel<S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVTile<S>::kBytes);
+        done = true;
+    }
+}
+
+int hv_tile2_occupancy(int storage, int media_mode) {
+    int blocks = 0;
+    with_storage(storage, [&](auto sc) {
+        with_media(media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            hv_tile2_prepare<S, M>();
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, hv_tile2_kernel<S, M>, kTileThreads,
+                                                          HVTile<S>::kBytes);
+        });
+    });
+    return blocks;
+}
+
+int hv_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st) {
+    const dim3 grid(T.tiles_x * T.tiles_y, (aA.g.nz + T.chunk - 1) / T.chunk);
+    with_storage(aA.storage, [&](auto sc) {
+        with_media(aA.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            hv_tile2_prepare<S, M>();
+            hv_tile2_kernel<S, M><<<grid, kTileThreads, HVTile<S>::kBytes, st>>>(aA, aB, T);
         });
     });
     return 1;

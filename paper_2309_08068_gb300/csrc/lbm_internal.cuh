@@ -809,6 +809,67 @@ __device__ inline void fused_loop(const FusedArgs& F, int nx, int nxy, int nz, D
     }
 }
 
+// --- two time steps per pass in shared memory (overlapped tiles) ------------------------------
+// A block owns a tile of kTileTX x kTileTY cells of each plane of a chunk of planes, and one thread
+// per cell of the tile and of a ring of one cell around it: kTileEX x kTileEY = (TX + 2) x (TY + 2)
+// "extended" cells. Marching up its chunk, it steps plane p of the extended tile (phase A, step t:
+// pulls from the A/B buffer in HBM, results into shared memory), then plane p - 1 of the tile
+// itself (phase B, step t + 1: pulls from the shared planes p - 2, p - 1, p, results into the other
+// A/B buffer). The ring is what phase B's pulls reach outside the tile, so blocks never wait for
+// one another; the ring's cells are stepped twice (by this block and by their own), the price of
+// that independence. The intermediate step never leaves the SM: each pair of steps reads and writes
+// the populations in HBM once, and writes them into L2 only twice (the fill and the output).
+// Phase B pulls a direction with v_z = +1 from plane p - 2, v_z = 0 from p - 1, v_z = -1 from p, so
+// shared memory keeps each plane's directions by v_z class only as long as they are read: the
+// v_z = -1 class of the newest plane, the v_z = 0 class of the last two and the v_z = +1 class of
+// the last three. A tile recomputes the source cells of its extended cells after its ordinary
+// update (after a barrier, so that their values replace the ordinary ones). The arithmetic is the
+// single step's, so a pass equals two single steps bit for bit.
+constexpr int kTileEX = 16, kTileEY = 16;  // extended tile: one thread per cell
+constexpr int kTileTX = kTileEX - 2, kTileTY = kTileEY - 2;
+constexpr int kTileThreads = kTileEX * kTileEY;
+
+struct TileArgs {
+    int tiles_x, tiles_y;  // tiles per plane along x and y (a ragged last tile covers the rest)
+    int chunk;             // planes per block; blockIdx.y selects the chunk
+    const int* entry_off;  // tiles_x tiles_y nz + 1 offsets into entries, by (tile, plane)
+    const int2* entries;   // (special-cell index m, extended-tile position) of every source cell of the
+                           // tile's extended cells, by tile then plane
+};
+
+// Where this thread's extended cell lies. Positions wrap periodically; a ragged last tile's core
+// positions past the lattice's edge are not its own (the first tile steps those cells).
+struct TileCell {
+    int tile, bx, by;
+    int cxy;   // x + nx y of the thread's extended cell
+    bool core;
+    int z0, z1;  // the block's planes
+};
+
+__host__ __device__ __forceinline__ bool tile_core(int local, int bx, int by, int nx, int ny) {
+    const int ex = local % kTileEX, ey = local / kTileEX;
+    return ex >= 1 && ex <= kTileTX && ey >= 1 && ey <= kTileTY && bx * kTileTX + ex - 1 < nx &&
+           by * kTileTY + ey - 1 < ny;
+}
+
+__host__ __device__ __forceinline__ int tile_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Lattice x (or y) of extended position e of tile b.
+__host__ __device__ __forceinline__ int tile_coord(int b, int e, int t, int n) { return tile_wrap(b * t - 1 + e, n); }
+
+__device__ __forceinline__ TileCell tile_cell(const Geometry& g, const TileArgs& T) {
+    TileCell c;
+    c.tile = blockIdx.x;
+    c.by = blockIdx.x / T.tiles_x;
+    c.bx = blockIdx.x - c.by * T.tiles_x;
+    const int ex = threadIdx.x % kTileEX, ey = threadIdx.x / kTileEX;
+    c.cxy = tile_coord(c.bx, ex, kTileTX, g.nx) + g.nx * tile_coord(c.by, ey, kTileTY, g.ny);
+    c.core = tile_core(threadIdx.x, c.bx, c.by, g.nx, g.ny);
+    c.z0 = blockIdx.y * T.chunk;
+    c.z1 = min(c.z0 + T.chunk, g.nz);
+    return c;
+}
+
 // --- host-side launchers (one set per model) -----------------------------------------------
 // Each returns the number of kernels it enqueued (errors are read with cudaGetLastError).
 int mm_launch_step(const StepArgs& a, cudaStream_t st);
@@ -866,6 +927,12 @@ int hv_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F,
 // Resident blocks per SM of the two-step kernel.
 int mm_fused2_occupancy(int storage, int media_mode);
 int hv_fused2_occupancy(int storage, int media_mode);
+// Two steps in one pass over shared-memory tiles: aA is step t, aB step t + 1; T the tiling. Returns
+// launches. _occupancy: resident blocks per SM.
+int mm_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st);
+int hv_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st);
+int mm_tile2_occupancy(int storage, int media_mode);
+int hv_tile2_occupancy(int storage, int media_mode);
 int hv_launch_record_step(const StepArgs& a, cudaStream_t st);
 int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
 int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st);

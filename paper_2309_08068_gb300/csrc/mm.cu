@@ -520,6 +520,112 @@ __global__ void __launch_bounds__(kFusedThreads, 3) mm_fused2_kernel(StepArgs aA
 }
 
 // ---------------------------------------------------------------------------------------------
+// Two steps per pass over shared-memory tiles (see TileArgs). Directions by v_z: class 0 (in-plane,
+// d = 0..3), class 1 (v_z = +1: d = 4, 5, 8, 9), class 2 (v_z = -1: d = 6, 7, 10, 11); four
+// directions per class.
+__host__ __device__ constexpr int mm_zclass(int d) { return d < 4 ? 0 : (((d >> 1) & 1) ? 2 : 1); }
+__host__ __device__ constexpr int mm_zrank(int d) { return d < 4 ? d : (d & 1) + (d >= 8 ? 2 : 0); }
+static_assert(mm_zclass(4) == 1 && mm_zclass(9) == 1 && mm_zclass(6) == 2 && mm_zclass(11) == 2 &&
+                  mm_zrank(8) == 2 && mm_zrank(10) == 2 && mm_zrank(7) == 1,
+              "v_z classes of the D3Q13 velocity table");
+
+// Six slots of 4 directions x kTileThreads cells: slot 0 the class-2 directions of the newest
+// plane, slots 1-2 class 0 of the last two planes, slots 3-5 class 1 of the last three.
+template <int S>
+struct MMTile {
+    using T = typename Pack4<S>::T;
+    static constexpr size_t kBytes = 6 * 4 * kTileThreads * sizeof(T);
+    T* base;
+    __device__ T* slot(int cls, int p) const {  // plane p >= -1
+        const int s = cls == 2 ? 0 : (cls == 0 ? 1 + (p + 3) % 2 : 3 + (p + 3) % 3);
+        return base + (size_t)s * 4 * kTileThreads;
+    }
+};
+
+// Phase A: pulls from the A/B buffer, results into the tile's slots of plane p.
+template <int S>
+struct MMToTile : NoStash {
+    using T = typename Pack4<S>::T;
+    T* dst[3];  // slots of plane p, by class
+    int local;  // extended-tile position of the cell
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) const {
+        mm_pull<S>(a, h, f);
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int d, int, float4 v) const {
+        dst[mm_zclass(d)][mm_zrank(d) * kTileThreads + local] = Pack4<S>::pack(v, a.scale);
+    }
+};
+
+// Phase B: pulls from the tile (class 0 from plane q, class 1 from q - 1, class 2 from q + 1),
+// results into the other A/B buffer.
+template <int S>
+struct MMFromTile : NoStash {
+    using T = typename Pack4<S>::T;
+    const T* src[3];
+    int local;
+    template <int S2>
+    __device__ void pull(const StepArgs& a, const Neighbourhood&, float4 (&f)[12]) const {
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            static_assert(kMMV[d][2] == (mm_zclass(d) == 0 ? 0 : (mm_zclass(d) == 1 ? 1 : -1)), "class of d");
+            constexpr int off = mm_zrank(d) * kTileThreads - (kMMV[d][0] + kMMV[d][1] * kTileEX);
+            f[d] = Pack4<S>::unpack(src[mm_zclass(d)][off + local], a.inv_scale);
+        });
+    }
+    template <int S2>
+    __device__ void put(const StepArgs& a, int d, int i, float4 v) const {
+        T* __restrict__ fout = static_cast<T*>(a.fout);
+        __stcs(fout + (size_t)d * a.g.n + i, Pack4<S>::pack(v, a.scale));
+    }
+};
+
+template <int S, int M>
+__global__ void __launch_bounds__(kTileThreads, S == kF32 ? 2 : 3) mm_tile2_kernel(StepArgs aA, StepArgs aB,
+                                                                                    TileArgs T) {
+    using TT = typename Pack4<S>::T;
+    extern __shared__ __align__(16) unsigned char mm_tile_smem[];
+    const MMTile<S> tile{reinterpret_cast<TT*>(mm_tile_smem)};
+    const int nz = aA.g.nz, nxy = aA.g.nx * aA.g.ny;
+    const TileCell c = tile_cell(aA.g, T);
+    const int* off = T.entry_off + (size_t)c.tile * nz;
+    for (int p = c.z0 - 1; p <= c.z1; ++p) {
+        const int pz = tile_wrap(p, nz);
+        {  // phase A: step t of the extended tile's cells of plane pz
+            const MMToTile<S> io{{}, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)}, (int)threadIdx.x};
+            mm_update<S, M, false, false, false>(aA, pz * nxy + c.cxy, 0, io);
+            const int lo = off[pz], hi = off[pz + 1];
+            if (hi > lo) {  // the source cells among them replace their ordinary update
+                __syncthreads();
+                for (int k = lo + threadIdx.x; k < hi; k += kTileThreads) {
+                    const int2 e = T.entries[k];
+                    const MMToTile<S> sio{{}, {io.dst[0], io.dst[1], io.dst[2]}, e.y};
+                    mm_update<S, M, true, false, false>(aA, aA.sv.cell[e.x], e.x, sio);
+                }
+            }
+        }
+        __syncthreads();
+        if (p > c.z0) {  // phase B: step t + 1 of the tile's own cells of plane q = p - 1
+            const int q = p - 1;
+            const MMFromTile<S> io{{}, {tile.slot(0, q), tile.slot(1, q - 1), tile.slot(2, q + 1)}, (int)threadIdx.x};
+            if (c.core) mm_update<S, M, false, false, false>(aB, q * nxy + c.cxy, 0, io);
+            const int lo = off[q], hi = off[q + 1];
+            if (hi > lo) {
+                __syncthreads();
+                for (int k = lo + threadIdx.x; k < hi; k += kTileThreads) {
+                    const int2 e = T.entries[k];
+                    if (!tile_core(e.y, c.bx, c.by, aA.g.nx, aA.g.ny)) continue;
+                    const MMFromTile<S> sio{{}, {io.src[0], io.src[1], io.src[2]}, e.y};
+                    mm_update<S, M, true, false, false>(aB, aB.sv.cell[e.x], e.x, sio);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Adjoint of one MM step. With per-velocity adjoints (a0^, a1^, c0^, c1^) of the post-collision
 // values, the transpose of eq. CollisionMiller through eq. equilibriumsMiller is
 //   adjoint of 2s_d = a0^ + a1^ + c0^ + c1^,  of 2 alpha_d = a0^ - a1^,  of 2 beta_d = c0^ - c1^,
@@ -820,6 +926,40 @@ int mm_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F,
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             mm_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
+        });
+    });
+    return 1;
+}
+
+template <int S, int M>
+void mm_tile2_prepare() {
+    static bool done = false;  // the attribute is a property of the kernel: set it once per process
+    if (!done) {
+        cudaFuncSetAttribute(mm_tile2_kernel<S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMTile<S>::kBytes);
+        done = true;
+    }
+}
+
+int mm_tile2_occupancy(int storage, int media_mode) {
+    int blocks = 0;
+    with_storage(storage, [&](auto sc) {
+        with_media(media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            mm_tile2_prepare<S, M>();
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mm_tile2_kernel<S, M>, kTileThreads,
+                                                          MMTile<S>::kBytes);
+        });
+    });
+    return blocks;
+}
+
+int mm_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st) {
+    const dim3 grid(T.tiles_x * T.tiles_y, (aA.g.nz + T.chunk - 1) / T.chunk);
+    with_storage(aA.storage, [&](auto sc) {
+        with_media(aA.media_mode, [&](auto mc) {
+            constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
+            mm_tile2_prepare<S, M>();
+            mm_tile2_kernel<S, M><<<grid, kTileThreads, MMTile<S>::kBytes, st>>>(aA, aB, T);
         });
     });
     return 1;

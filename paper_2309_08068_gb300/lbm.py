@@ -98,6 +98,7 @@ def load_library(path: str | None = None):
         "lbm_step_fusion_active": (I, [P]),
         "lbm_set_wait_limit": (I, [P, ctypes.c_longlong]),
         "lbm_fused_schedule_check": (I, [I, I, I, I, I, I]),
+        "lbm_tiled_layout_check": (I, [I, I]),
         "lbm_halo_bytes": (I64, [P]),
         "lbm_halo_pack": (I, [P, I, P, I]),
         "lbm_halo_unpack": (I, [P, I, P, I]),
@@ -341,9 +342,10 @@ class Lattice:
 
     # -- two steps per pass ----------------------------------------------------------------------
     def set_step_fusion(self, mode: int, tile_cells: int = 0) -> None:
-        """0: one launch per step; 1 (default): pairs of steps as one pass when its intermediate
-        planes fit in L2; 2: whenever the lattice allows it. tile_cells: cells per work item of a
-        pass (multiple of 256; 0 keeps the current value) (lbm_set_step_fusion)."""
+        """0: one launch per step; 1 (default): pairs of steps as one pass, the tiled pass where it
+        applies, else the L2-ring pass where it fits; 2: the ring pass wherever it applies; 3: the
+        tiled pass wherever it applies. tile_cells: cells per work item of the ring pass (multiple of
+        256; 0 keeps the current value) (lbm_set_step_fusion)."""
         self._check(self.lib.lbm_set_step_fusion(self.h, int(mode), int(tile_cells)))
 
     def set_wait_limit(self, ns: int) -> None:
@@ -353,10 +355,15 @@ class Lattice:
 
     @property
     def step_fusion_active(self) -> bool:
+        return self.pass_kind is not None
+
+    @property
+    def pass_kind(self):
+        """The pass lbm_step would run pairs of steps as: "tiled", "ring", or None for single steps."""
         rc = int(self.lib.lbm_step_fusion_active(self.h))
         if rc < 0:
             self._check(rc)
-        return rc == 1
+        return {0: None, 1: "ring", 2: "tiled"}[rc]
 
     # -- z-slab halo (z_ghost lattices) ---------------------------------------------------------
     @property

@@ -137,7 +137,7 @@ def test_batch_runs_wide_lattices_as_two_step_passes(model):
         return out
 
     solo, grouped = lattices(), lattices()
-    assert [L.step_fusion_active for L in grouped] == [True, True, False, False]
+    assert [L.pass_kind for L in grouped] == [{"mm": "tiled", "hv": "ring"}[model]] * 2 + [None, None]
     batch = Batch(grouped)
     for rep in range(2):
         for L, n in zip(solo, steps):

@@ -104,23 +104,36 @@ def test_fused_pairs_match_the_oracle(model):
 
 def test_fusion_switches_on_only_where_allowed():
     from paper_2309_08068_gb300.lbm import Lattice
-    def active(shape, mode=1, **kw):
+    def kind(shape, mode=1, **kw):
         L = Lattice("mm", shape, **kw)
         L.set_step_fusion(mode)
-        a = L.step_fusion_active
+        k = L.pass_kind
         L.close()
-        return a
-    assert active(PLANE + (11,))                          # 7 planes of 7.9 MB fit in L2
-    assert not active(PLANE + (11,), mode=0)
-    assert not active(PLANE + (11,), track_rho=True)      # rest populations are not in the ring
-    assert not active(PLANE + (11,), z_ghost=True)        # slabs step one plane range at a time
-    assert not active((64, 64, 11), mode=2)               # 4,096 cells per plane cannot fill the GPU
-    assert not active(PLANE + (3,), mode=2)               # MM runs A 3 planes ahead: nz >= 4
-    assert active(PLANE + (4,), mode=2)
-    assert not active((512, 512, 6))                      # 7 x 50 MB does not fit in L2
-    assert active((512, 512, 6), mode=2)
-    assert not active(PLANE + (11,), storage="f16", storage_scale=2.0 ** 12)  # single steps are faster
-    assert active(PLANE + (11,), mode=2, storage="bf16")
+        return k
+    assert kind(PLANE + (11,)) == "tiled"                 # MM, FP32, planes of at least 16 x 16
+    assert kind((64, 64, 11)) == "tiled"
+    assert kind((16, 16, 3)) == "tiled"
+    assert kind((15, 64, 11)) is None                      # a 16-wide extended tile needs nx >= 16
+    assert kind((64, 64, 2)) is None                       # and nz >= 3
+    L = Lattice("hv", PLANE + (11,))                       # HV takes the ring pass by default
+    assert L.pass_kind == "ring"
+    L.set_step_fusion(3)
+    assert L.pass_kind == "tiled"
+    L.close()
+    L = Lattice("hv", (64, 64, 11))                        # and single steps where the ring does not apply
+    assert L.pass_kind is None
+    L.close()
+    assert kind(PLANE + (11,), mode=0) is None
+    assert kind(PLANE + (11,), track_rho=True) is None    # rest populations are not carried
+    assert kind(PLANE + (11,), z_ghost=True) is None      # slabs step one plane range at a time
+    assert kind(PLANE + (11,), mode=2) == "ring"          # 7 planes of 7.9 MB fit in L2
+    assert kind((64, 64, 11), mode=2) is None             # 4,096 cells per plane cannot fill the GPU
+    assert kind(PLANE + (3,), mode=2) is None             # MM runs A 3 planes ahead: nz >= 4
+    assert kind(PLANE + (4,), mode=2) == "ring"
+    assert kind((512, 512, 6), mode=2) == "ring"          # forced: 7 x 50 MB exceed L2
+    assert kind(PLANE + (11,), storage="f16", storage_scale=2.0 ** 12) is None  # single steps by default
+    assert kind(PLANE + (11,), mode=3, storage="f16", storage_scale=2.0 ** 12) == "tiled"
+    assert kind(PLANE + (11,), mode=2, storage="bf16") == "ring"
 
 
 def test_hv_needs_five_planes():
@@ -135,7 +148,7 @@ def test_hv_needs_five_planes():
 def test_fusion_mode_is_checked():
     from paper_2309_08068_gb300.lbm import Lattice, LbmError
     L = Lattice("hv", (8, 8, 8))
-    for mode, tile in ((3, 0), (-1, 0), (1, 100), (1, 8192), (1, -256)):
+    for mode, tile in ((4, 0), (-1, 0), (1, 100), (1, 8192), (1, -256)):
         with pytest.raises(LbmError):
             L.set_step_fusion(mode, tile)
     L.close()
@@ -211,3 +224,76 @@ def test_fused_pairs_equal_single_steps_with_full_source_planes(model, tile):
     assert active
     _, single = run(w, f, 5, 0)
     assert_same(fused, single, q)
+
+
+
+# ---------------------------------------------------------------------------------------------
+# The tiled pass (mode 3; the default for FP32): shared-memory tiles with a one-cell ring
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("media", ["random", "few", "vacuum"])
+@pytest.mark.parametrize("shape", [(256, 160, 11), (29, 17, 9), (16, 16, 3), (45, 31, 40), (64, 48, 5)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_tiled_pairs_equal_single_steps(model, media, shape):
+    """Ragged last tiles in x and y (29 = 14 + 15, 45 = 3 x 14 + 3), the smallest plane and depth the
+    pass takes (16 x 16 x 3: the ring of a tile wraps onto its neighbour on both sides), several
+    chunks of planes per tile column (nz = 40), odd step counts, sources in every plane."""
+    w, f = wl.slab_case(model, shape, seed=170 + shape[2], media=media)
+    q = 48 if model == "mm" else 36
+    active, tiled = run(w, f, 7, 3)
+    assert active
+    _, single = run(w, f, 7, 0)
+    assert_same(tiled, single, q)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_tiled_pairs_equal_single_steps_in_16_bit_storage(model, storage):
+    w, f = wl.slab_case(model, (64, 40, 9), seed=175, amplitude=1e-3)
+    kw = dict(storage=storage, storage_scale=2.0 ** 12 if storage == "f16" else 0.0)
+    q = 48 if model == "mm" else 36
+    active, tiled = run(w, f, 6, 3, **kw)
+    assert active
+    _, single = run(w, f, 6, 0, **kw)
+    assert_same(tiled, single, q)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_tiled_pairs_with_full_source_planes(model):
+    """Whole planes of source cells: every extended cell of those planes is recomputed after the
+    ordinary update, in both phases, including the wrap plane 0."""
+    w, f = wl.random_state(model, (64, 48, 7), seed=176, media="few", n_sources=0)
+    nxy = 64 * 48
+    rng = np.random.default_rng(177)
+    c = wl.LIGHT_SPEED[model]
+    w.sources = [
+        wl.Source("impose", np.arange(nxy, dtype=np.int64), wl.TimeFunction("sin", 1.0, 40.0, 0.3),
+                  E0=(1e-3, 0.0, 0.0), B0=(0.0, 1e-3 / c, 0.0)),
+        wl.Source("current", np.arange(3 * nxy, 4 * nxy + nxy // 2, dtype=np.int64),
+                  wl.TimeFunction("sin", 1e-3, 17.0, 0.1), w=rng.standard_normal((nxy + nxy // 2, 3))),
+    ]
+    q = 48 if model == "mm" else 36
+    active, tiled = run(w, f, 5, 3)
+    assert active
+    _, single = run(w, f, 5, 0)
+    assert_same(tiled, single, q)
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_tiled_pairs_match_the_oracle(model):
+    w, f = wl.slab_case(model, (40, 33, 6), seed=178)
+    f = np.asarray(f, np.float32).astype(np.float64)
+    for attr in ("eps_r", "mu_r", "sigma"):
+        setattr(w, attr, np.asarray(getattr(w, attr), np.float32).astype(np.float64))
+    for s in w.sources:
+        if s.w is not None:
+            s.w = np.asarray(s.w, np.float32).astype(np.float64)
+        s.E0 = tuple(float(np.float32(v)) for v in s.E0)
+        s.B0 = tuple(float(np.float32(v)) for v in s.B0)
+    _, (pops, _, _) = run(w, f, 4, 3)
+    O = oracle_from_workload(w, init=False, threads=16)
+    O.set_populations(f, 0)
+    O.step(4)
+    q = 48 if model == "mm" else 36
+    assert rel_l2(pops[:q], O.populations()[:q]) <= 1e-5

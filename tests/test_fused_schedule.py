@@ -40,3 +40,17 @@ def test_invalid_shapes_are_rejected(lib):
     assert lib.lbm_fused_schedule_check(16, 16, 16, 2, 2, 256) < 0   # R < L + 1
     assert lib.lbm_fused_schedule_check(16, 16, 16, 5, 1, 256) < 0   # L < 2: B(k) would precede A(k+1)
     assert lib.lbm_fused_schedule_check(16, 16, 2, 5, 3, 256) < 0    # nz < 3
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (17, 16), (28, 28), (29, 30), (31, 45), (256, 256), (300, 137),
+                                   (208, 208), (1024, 16), (16, 999), (128, 128), (272, 272)])
+def test_tiled_pass_layout(lib, nx, ny):
+    """The tiled pass: an extended tile's 16 x 16 positions are distinct cells, a tile cell's
+    neighbours lie in its extended tile, and the tiles cover the plane once (ragged last tiles
+    included)."""
+    assert lib.lbm_tiled_layout_check(nx, ny) == 0
+
+
+def test_tiled_pass_layout_rejects_small_planes(lib):
+    assert lib.lbm_tiled_layout_check(15, 64) < 0
+    assert lib.lbm_tiled_layout_check(64, 15) < 0
