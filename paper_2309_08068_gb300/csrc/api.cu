@@ -66,6 +66,7 @@ struct lbm_ctx {
     int* d_entry_src = nullptr;
     float* d_entry_w = nullptr;
     uint32_t* d_impose_mask = nullptr;
+    int* d_block_begin = nullptr;  // where each kBlock-cell block of the step range starts in d_cell
     // reductions
     double* d_partials = nullptr;
     double* d_result = nullptr;
@@ -159,6 +160,7 @@ StepArgs base_args(lbm_ctx* c) {
     a.sv.entry_src = c->d_entry_src;
     a.sv.entry_w = c->d_entry_w;
     a.sv.impose_mask = c->d_impose_mask;
+    a.sv.block_begin = c->d_block_begin;
     for (size_t k = 0; k < c->sources.size(); ++k) {
         for (int q = 0; q < 3; ++q) {
             a.sc.E0[k][q] = c->sources[k].E0[q];
@@ -486,6 +488,7 @@ void free_sources_device(lbm_ctx* c) {
     free_dev(c->d_entry_src);
     free_dev(c->d_entry_w);
     free_dev(c->d_impose_mask);
+    free_dev(c->d_block_begin);
     c->n_special = 0;
 }
 
@@ -547,6 +550,22 @@ int rebuild_sources(lbm_ctx* c) {
         CUDA_TRY(c, cudaMemcpy(c->d_entry_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice));
     }
     CUDA_TRY(c, cudaMemcpy(c->d_impose_mask, mask.data(), sizeof(uint32_t) * ns, cudaMemcpyHostToDevice));
+    // where each block of kBlock cells of the step range starts in the sorted list: a step launch
+    // recomputes a block's source cells at the end of the block
+    const int r0 = c->z_ghost ? c->g.nx * c->g.ny : 0, r1 = c->z_ghost ? c->g.n - c->g.nx * c->g.ny : c->g.n;
+    const int nb = (r1 - r0 + kBlock - 1) / kBlock;
+    std::vector<int> bb((size_t)nb + 1);
+    for (int b = 0, k = 0; b <= nb; ++b) {
+        const long long start = std::min<long long>((long long)r0 + (long long)b * kBlock, r1);
+        while (k < ns && cell[(size_t)k] < start) ++k;
+        bb[(size_t)b] = k;
+    }
+    if (cudaMalloc(&c->d_block_begin, sizeof(int) * bb.size()) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_block_begin = nullptr;
+        return fail(c, LBM_ENOMEM, "cannot allocate the blocks' source-cell offsets");
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_block_begin, bb.data(), sizeof(int) * bb.size(), cudaMemcpyHostToDevice));
     c->n_special = ns;
     c->h_cell = cell;
     return LBM_OK;
@@ -1831,17 +1850,39 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
     launched += ctx->model == LBM_MM ? mm_launch_adjoint_terminal(A, n_plane, ctx->stream)
                                      : hv_launch_adjoint_terminal(A, n_plane, ctx->stream);
     // Backward through the segment of steps first .. first + len - 1, whose records are in slots
-    // 0 .. len - 1.
+    // 0 .. len - 1. With fusion mode 3, pairs of MM backward steps run as tiled passes (same
+    // arithmetic and order of the gradient sums: the same bits). It is not the default: on GB300
+    // (128^3, per-cell eps_r) a tiled pair takes 296 us against 2 x 141 for single steps.
+    const bool tiled_back = ctx->model == LBM_MM && ctx->fusion == 3 && pass_kind(ctx) == kPassTiled;
+    if (tiled_back && (rc = ensure_tiled(ctx)) != LBM_OK) return rc;
+    TileArgs TA{};
+    if (tiled_back) {
+        TA.tiles_x = tiled_tiles_x(ctx);
+        TA.tiles_y = tiled_tiles_y(ctx);
+        TA.chunk = tiled_chunk(ctx);
+        TA.entry_off = ctx->d_tiled_off;
+        TA.entries = ctx->d_tiled_entries;
+    }
+    auto step_args = [&](AdjointArgs& X, int first, int j) {  // the backward step of record slot j
+        const int64_t nstep = first + j;  // reverses forward iteration nstep + 1
+        X.a = base_args(ctx);
+        X.a.rec = reinterpret_cast<float*>(Ly.recs + rec_bytes * (size_t)j);
+        fill_scalars(ctx, X.a, t0 + nstep + 1);
+        X.loss_active = nstep >= 1 ? 1 : 0;
+    };
     auto backward = [&](int first, int len) {
         for (int j = len - 1; j >= 0; --j) {
-            const int64_t nstep = first + j;  // reverses forward iteration nstep + 1
-            A.a = base_args(ctx);
-            A.a.rec = reinterpret_cast<float*>(Ly.recs + rec_bytes * (size_t)j);
-            fill_scalars(ctx, A.a, t0 + nstep + 1);
+            step_args(A, first, j);
             state_ptrs(Ly.nu + state * (size_t)nu_cur, const_cast<void**>(&A.nu_in), const_cast<void**>(&A.nu_in2));
             state_ptrs(Ly.nu + state * (size_t)(1 - nu_cur), &A.nu_out, &A.nu_out2);
-            A.loss_active = nstep >= 1 ? 1 : 0;
-            launched += ctx->model == LBM_MM ? mm_launch_adjoint(A, ctx->stream) : hv_launch_adjoint(A, ctx->stream);
+            if (tiled_back && j >= 1) {
+                AdjointArgs A2 = A;  // the step of slot j - 1 writes nu_out; A reads nu_in
+                step_args(A2, first, j - 1);
+                launched += mm_launch_adjoint2(A, A2, TA, ctx->stream);
+                --j;
+            } else {
+                launched += ctx->model == LBM_MM ? mm_launch_adjoint(A, ctx->stream) : hv_launch_adjoint(A, ctx->stream);
+            }
             nu_cur = 1 - nu_cur;
         }
     };

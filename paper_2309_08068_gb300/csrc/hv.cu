@@ -422,17 +422,12 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 3 : 4) hv_tile2_kern
     }
 }
 
-template <int S, int M, bool kSpecial>
+// The block's source cells are recomputed at the end (block_source_cells).
+template <int S, int M>
 __global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
-    if constexpr (kSpecial) {
-        const int m = blockIdx.x * blockDim.x + threadIdx.x;
-        if (m >= a.sv.n_special) return;
-        hv_update<S, M, kSpecial>(a, a.sv.cell[m], m);
-    } else {
-        const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.cell_end) return;
-        hv_update<S, M, kSpecial>(a, i, 0);
-    }
+    const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.cell_end) hv_update<S, M, false>(a, i, 0);
+    block_source_cells(a.sv, blockIdx.x, [&](int c, int m) { hv_update<S, M, true>(a, c, m); });
 }
 
 // Equilibria for fields E, B and J = 0 (Appendix B initialisation), stored so that cell x pulls
@@ -591,17 +586,11 @@ __global__ void __launch_bounds__(kBlock) hv_batch_special_kernel(const BatchLat
     }
 }
 
-template <int M, bool kSpecial>
+template <int M>
 __global__ void __launch_bounds__(kBlock) hv_record_kernel(StepArgs a) {
-    if constexpr (kSpecial) {
-        const int m = blockIdx.x * blockDim.x + threadIdx.x;
-        if (m >= a.sv.n_special) return;
-        hv_update<kF32, M, true, true>(a, a.sv.cell[m], m);
-    } else {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.g.n) return;
-        hv_update<kF32, M, false, true>(a, i, 0);
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.g.n) hv_update<kF32, M, false, true>(a, i, 0);
+    block_source_cells(a.sv, blockIdx.x, [&](int c, int m) { hv_update<kF32, M, true, true>(a, c, m); });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -715,18 +704,13 @@ __device__ __forceinline__ void hv_adjoint_cell(const AdjointArgs& A, int i, int
     A.grad_sigma[i] = gsig_old + (gJ.x * F.E.x + gJ.y * F.E.y + gJ.z * F.E.z);
 }
 
+// Source cells (skipped by the ordinary update through the mask) are stepped back at the end of
+// their block (block_source_cells).
 template <int M>
 __global__ void __launch_bounds__(kBlock) hv_adjoint_kernel(AdjointArgs A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.a.g.n) return;
-    hv_adjoint_cell<M, false, false>(A, i, 0);
-}
-
-template <int M>
-__global__ void __launch_bounds__(kBlock) hv_adjoint_special_kernel(AdjointArgs A) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= A.a.sv.n_special) return;
-    hv_adjoint_cell<M, true, false>(A, A.a.sv.cell[m], m);
+    if (i < A.a.g.n) hv_adjoint_cell<M, false, false>(A, i, 0);
+    block_source_cells(A.a.sv, blockIdx.x, [&](int c, int m) { hv_adjoint_cell<M, true, false>(A, c, m); });
 }
 
 template <int M>
@@ -743,12 +727,8 @@ int hv_launch_step(const StepArgs& a, cudaStream_t st) {
     with_storage(a.storage, [&](auto sc) {
         with_media(a.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
-            hv_step_kernel<S, M, false><<<blocks_for(a.cell_end - a.cell_begin), kBlock, 0, st>>>(a);
+            hv_step_kernel<S, M><<<blocks_for(a.cell_end - a.cell_begin), kBlock, 0, st>>>(a);
             launched = 1;
-            if (a.sv.n_special > 0) {
-                hv_step_kernel<S, M, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
-                launched = 2;
-            }
         });
     });
     return launched;
@@ -840,10 +820,6 @@ int hv_launch_adjoint(const AdjointArgs& A, cudaStream_t st) {
         constexpr int M = decltype(mc)::value;
         hv_adjoint_kernel<M><<<blocks_for(A.a.g.n), kBlock, 0, st>>>(A);
         launched = 1;
-        if (A.a.sv.n_special > 0) {
-            hv_adjoint_special_kernel<M><<<blocks_for(A.a.sv.n_special), kBlock, 0, st>>>(A);
-            launched = 2;
-        }
     });
     return launched;
 }
@@ -923,12 +899,8 @@ int hv_launch_record_step(const StepArgs& a, cudaStream_t st) {
     int launched = 0;
     with_media(a.media_mode, [&](auto mc) {
         constexpr int M = decltype(mc)::value;
-        hv_record_kernel<M, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+        hv_record_kernel<M><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
         launched = 1;
-        if (a.sv.n_special > 0) {
-            hv_record_kernel<M, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
-            launched = 2;
-        }
     });
     return launched;
 }

@@ -67,7 +67,23 @@ struct SourceView {
     const int* entry_src;       // source slot of each current entry
     const float* entry_w;       // 3 weights per current entry
     const uint32_t* impose_mask;  // bit k set: source slot k imposes fields at this cell
+    const int* block_begin;       // [blocks + 1] for the blocks of kBlock cells of the step range
+                                  // [cell_begin, cell_end): where each block's cells start in `cell`
+                                  // (null without source cells)
 };
+
+// The source cells of block `b` of a launch over the step range (one thread per cell), recomputed
+// after the block's ordinary updates: a barrier, so that their values replace the ordinary ones,
+// then update(i, m) for every source cell i = cell[m] of the block. Every thread of the block must
+// call this (the barrier), whether or not it had a cell of its own.
+template <class Update>
+__device__ __forceinline__ void block_source_cells(const SourceView& sv, int b, Update&& update) {
+    if (!sv.block_begin) return;
+    const int lo = sv.block_begin[b], hi = sv.block_begin[b + 1];
+    if (hi <= lo) return;
+    __syncthreads();
+    for (int m = lo + (int)threadIdx.x; m < hi; m += (int)blockDim.x) update(sv.cell[m], m);
+}
 
 // Per-step source values s_k(t) and the constant imposed-field vectors of each slot.
 struct SourceScalars {
@@ -326,6 +342,7 @@ struct CellSource {
     bool imposed;
 };
 
+// The sums are explicit fused multiply-adds, so that every kernel that inlines this gets the same bits.
 __device__ __forceinline__ CellSource cell_source(const SourceView& sv, const SourceScalars& sc, int m) {
     CellSource cs;
     cs.J = make_float3(0.f, 0.f, 0.f);
@@ -334,21 +351,21 @@ __device__ __forceinline__ CellSource cell_source(const SourceView& sv, const So
     const int b = sv.entry_begin[m], e = sv.entry_begin[m + 1];
     for (int k = b; k < e; ++k) {
         const float s = sc.s[sv.entry_src[k]];
-        cs.J.x += sv.entry_w[3 * k + 0] * s;
-        cs.J.y += sv.entry_w[3 * k + 1] * s;
-        cs.J.z += sv.entry_w[3 * k + 2] * s;
+        cs.J.x = __fmaf_rn(sv.entry_w[3 * k + 0], s, cs.J.x);
+        cs.J.y = __fmaf_rn(sv.entry_w[3 * k + 1], s, cs.J.y);
+        cs.J.z = __fmaf_rn(sv.entry_w[3 * k + 2], s, cs.J.z);
     }
     const uint32_t mask = sv.impose_mask[m];
     cs.imposed = mask != 0u;
     for (int k = 0; k < kMaxSources; ++k) {
         if ((mask >> k) & 1u) {
             const float s = sc.s[k];
-            cs.E.x += sc.E0[k][0] * s;
-            cs.E.y += sc.E0[k][1] * s;
-            cs.E.z += sc.E0[k][2] * s;
-            cs.B.x += sc.B0[k][0] * s;
-            cs.B.y += sc.B0[k][1] * s;
-            cs.B.z += sc.B0[k][2] * s;
+            cs.E.x = __fmaf_rn(sc.E0[k][0], s, cs.E.x);
+            cs.E.y = __fmaf_rn(sc.E0[k][1], s, cs.E.y);
+            cs.E.z = __fmaf_rn(sc.E0[k][2], s, cs.E.z);
+            cs.B.x = __fmaf_rn(sc.B0[k][0], s, cs.B.x);
+            cs.B.y = __fmaf_rn(sc.B0[k][1], s, cs.B.y);
+            cs.B.z = __fmaf_rn(sc.B0[k][2], s, cs.B.z);
         }
     }
     return cs;
@@ -935,6 +952,9 @@ int mm_tile2_occupancy(int storage, int media_mode);
 int hv_tile2_occupancy(int storage, int media_mode);
 int hv_launch_record_step(const StepArgs& a, cudaStream_t st);
 int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
+// Two MM backward steps in one pass over shared-memory tiles: A1 the step of nu^{n+1} -> nu^n (its
+// nu_in is read), A2 the step nu^n -> nu^{n-1} (its nu_out is written); T the tiled pass's tiling.
+int mm_launch_adjoint2(const AdjointArgs& A1, const AdjointArgs& A2, const TileArgs& T, cudaStream_t st);
 int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st);
 int hv_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
 int hv_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st);

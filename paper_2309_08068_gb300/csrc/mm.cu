@@ -3,10 +3,10 @@
 // One thread updates one cell. The 48 moving populations arrive as 12 vector pulls (one per D3Q13
 // velocity; the four values of a velocity move together: a float4, or 8 bytes with 16-bit storage),
 // the whole collision runs in FP32 registers, and the 12 results are stored at the cell (pull
-// scheme). Sources and imposed
-// cells are handled by a second, small launch over the merged source-cell list that recomputes
-// those cells with their current and imposed fields and overwrites them; the main launch stays
-// branch-free.
+// scheme). The ordinary update is branch-free; source and imposed cells are recomputed afterwards
+// with their current and imposed fields, overwriting the ordinary result: at the end of their
+// block in the single-step kernels (block_source_cells), in their tile in the two-step passes, and
+// by a second small launch over the merged source-cell list in the batched kernels.
 //
 // Direction tables. Direction d = p*4 + (i-1) with the plane p and index i of eq.
 // VelocitySetMiller: v_i^p = sqrt(2) (cos((2i-1) pi/4), sin((2i-1) pi/4)) in the xy (p = 0), xz
@@ -210,17 +210,12 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m, const
 // 3 resident blocks for FP32 storage; 4 for 16-bit storage, whose halved bytes need more loads in
 // flight per SM to reach the copy bandwidth (256^3 dipole on GB300, BF16: 0.475 against 0.497 ms
 // per step at 3 blocks).
-template <int S, int M, bool kSpecial, bool kRho>
+// The block's source cells are recomputed at the end (block_source_cells).
+template <int S, int M, bool kRho>
 __global__ void __launch_bounds__(kBlock, S == kF32 ? 3 : 4) mm_step_kernel(StepArgs a) {
-    if constexpr (kSpecial) {
-        const int m = blockIdx.x * blockDim.x + threadIdx.x;
-        if (m >= a.sv.n_special) return;
-        mm_update<S, M, kSpecial, kRho>(a, a.sv.cell[m], m);
-    } else {
-        const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.cell_end) return;
-        mm_update<S, M, kSpecial, kRho>(a, i, 0);
-    }
+    const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.cell_end) mm_update<S, M, false, kRho>(a, i, 0);
+    block_source_cells(a.sv, blockIdx.x, [&](int c, int m) { mm_update<S, M, true, kRho>(a, c, m); });
 }
 
 // Equilibrium populations of cell x for fields E, B and J = 0 (Appendix B initialisation).
@@ -409,17 +404,11 @@ __global__ void __launch_bounds__(kBlock) mm_batch_special_kernel(const BatchLat
     }
 }
 
-template <int M, bool kSpecial, bool kRho>
+template <int M, bool kRho>
 __global__ void __launch_bounds__(kBlock, 3) mm_record_kernel(StepArgs a) {
-    if constexpr (kSpecial) {
-        const int m = blockIdx.x * blockDim.x + threadIdx.x;
-        if (m >= a.sv.n_special) return;
-        mm_update<kF32, M, true, kRho, true>(a, a.sv.cell[m], m);
-    } else {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= a.g.n) return;
-        mm_update<kF32, M, false, kRho, true>(a, i, 0);
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.g.n) mm_update<kF32, M, false, kRho, true>(a, i, 0);
+    block_source_cells(a.sv, blockIdx.x, [&](int c, int m) { mm_update<kF32, M, true, kRho, true>(a, c, m); });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -639,8 +628,34 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 2 : 3) mm_tile2_kern
 //   dL/d sigma += gJ . E - gDpp . X * g^2 / (2 eps_r).
 // Imposed cells output f_eq(E_imp, B_imp, 0): nothing flows back to f, and
 // d alpha_d / d eps_r = e_h . E_imp / 8. The plane loss |E|^2 adds 2E to gE.
-template <int M, bool kSpecial, bool kTerminal>
-__device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int m) {
+// Where a backward step reads lambda and writes nu^n, and what it does with the cell's loss and
+// gradient terms: the single-step kernels read nu^{n+1} from the adjoint buffer, write nu^n back to
+// one, and add the gradient terms to the per-cell sums in memory.
+struct MMAdjGlobal {
+    __device__ bool counts() const { return true; }  // the cell's loss and gradient terms count here
+    __device__ void lam(const AdjointArgs& A, const Neighbourhood& h, float4 (&lam)[12]) const {
+        const int n = A.a.g.n;
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            const int dst = shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h);
+            lam[d] = __ldg(static_cast<const float4*>(A.nu_in) + (size_t)d * n + dst);
+        });
+    }
+    __device__ void put_nu(const AdjointArgs& A, int d, int i, float4 o) const {
+        static_cast<float4*>(A.nu_out)[(size_t)d * A.a.g.n + i] = o;
+    }
+    __device__ void grad_load(const AdjointArgs& A, int i, float& ge, float& gs) const {
+        ge = __ldg(&A.grad_eps[i]);
+        gs = __ldg(&A.grad_sigma[i]);
+    }
+    __device__ void grad_store(const AdjointArgs& A, int i, float ge, float gs) const {
+        A.grad_eps[i] = ge;
+        A.grad_sigma[i] = gs;
+    }
+};
+
+template <int M, bool kSpecial, bool kTerminal, class IO = MMAdjGlobal>
+__device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int m, const IO& io = IO{}) {
     const StepArgs& a = A.a;
     const int n = a.g.n;
     const Neighbourhood h = neighbourhood(a.g, i);
@@ -654,7 +669,9 @@ __device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int
     // Every load is issued up front: the source-cell mask of the main launch only gates the stores,
     // so it adds no round trip before the others.
     const bool skip = !kSpecial && !kTerminal && A.special_mask[i] != 0;
-    const float geps_old = __ldg(&A.grad_eps[i]), gsig_old = __ldg(&A.grad_sigma[i]);
+    const bool counts = io.counts();
+    float geps_old = 0.f, gsig_old = 0.f;
+    if (counts) io.grad_load(A, i, geps_old, gsig_old);
     // E and X of f^n: from the forward step's record, or (terminal) from the final state
     float3 E, X;
     if constexpr (kTerminal) {
@@ -672,15 +689,11 @@ __device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int
     } F{E, X};
     const float inv_er = mat.c0.y, g = mat.c0.z, inv4mu = mat.c0.w, sigma = mat.c1.x;
     float4 lam[12];
-    static_for<0, 12>([&](auto dc) {
-        constexpr int d = decltype(dc)::value;
-        if constexpr (kTerminal) {
-            lam[d] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-            const int dst = shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h);
-            lam[d] = __ldg(static_cast<const float4*>(A.nu_in) + (size_t)d * n + dst);
-        }
-    });
+    if constexpr (kTerminal) {
+        static_for<0, 12>([&](auto dc) { lam[decltype(dc)::value] = make_float4(0.f, 0.f, 0.f, 0.f); });
+    } else {
+        io.lam(A, h, lam);
+    }
     float gJx = 0.f, gJy = 0.f, gJz = 0.f, gAx = 0.f, gAy = 0.f, gAz = 0.f, gEx = 0.f, gEy = 0.f, gEz = 0.f;
     float gBx = 0.f, gBy = 0.f, gBz = 0.f, geps_imposed = 0.f;
     if (!imposed) {
@@ -717,13 +730,13 @@ __device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int
         gEx = __fmaf_rn(2.f, F.E.x, gEx);
         gEy = __fmaf_rn(2.f, F.E.y, gEy);
         gEz = __fmaf_rn(2.f, F.E.z, gEz);
-        add_plane_loss<kTerminal>(A, h, F.E);
+        if (counts) add_plane_loss<kTerminal>(A, h, F.E);
     }
     const float gDx = __fmaf_rn(gEx, inv_er, 0.25f * gAx), gDy = __fmaf_rn(gEy, inv_er, 0.25f * gAy),
                 gDz = __fmaf_rn(gEz, inv_er, 0.25f * gAz);
-    const float gXx = g * gDx, gXy = g * gDy, gXz = g * gDz;
-    if (skip) return;  // a source cell: the second launch writes it
-    float4* nu_out = static_cast<float4*>(A.nu_out);
+    // __fmul_rn: the products must not fuse into the sums below differently in different kernels
+    const float gXx = __fmul_rn(g, gDx), gXy = __fmul_rn(g, gDy), gXz = __fmul_rn(g, gDz);
+    if (skip) return;  // a source cell: the source-cell pass writes it
     static_for<0, 12>([&](auto dc) {
         constexpr int d = decltype(dc)::value;
         const float gde = 0.5f * sdot<kMMEh[d][0], kMMEh[d][1], kMMEh[d][2]>(gXx, gXy, gXz);
@@ -731,30 +744,133 @@ __device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int
         float4 o;
         if (imposed) o = make_float4(gde, -gde, gdb, -gdb);
         else o = make_float4(gde - lam[d].x, -gde - lam[d].y, gdb - lam[d].z, -gdb - lam[d].w);
-        nu_out[(size_t)d * n + i] = o;
+        io.put_nu(A, d, i, o);
     });
-    const float gEdotE = gEx * F.E.x + gEy * F.E.y + gEz * F.E.z;
-    const float gDdotX = gDx * F.X.x + gDy * F.X.y + gDz * F.X.z;
+    if (!counts) return;
+    // Explicit fused multiply-adds wherever a product meets an addition: the single-step and the
+    // tiled backward kernels inline this code in different contexts and must agree bit for bit.
+    const float gEdotE = __fmaf_rn(gEz, F.E.z, __fmaf_rn(gEy, F.E.y, __fmul_rn(gEx, F.E.x)));
+    const float gDdotX = __fmaf_rn(gDz, F.X.z, __fmaf_rn(gDy, F.X.y, __fmul_rn(gDx, F.X.x)));
+    const float gJdotE = __fmaf_rn(gJz, F.E.z, __fmaf_rn(gJy, F.E.y, __fmul_rn(gJx, F.E.x)));
     const float gg = g * g * inv_er;
-    float deps = geps_imposed - gEdotE * inv_er;
+    float deps = __fmaf_rn(-gEdotE, inv_er, geps_imposed);
     deps = __fmaf_rn(gDdotX, gg * 0.5f * sigma * inv_er, deps);
-    const float dsig = __fmaf_rn(-gDdotX, 0.5f * gg, gJx * F.E.x + gJy * F.E.y + gJz * F.E.z);
-    A.grad_eps[i] = geps_old + deps;
-    A.grad_sigma[i] = gsig_old + dsig;
+    const float dsig = __fmaf_rn(-gDdotX, 0.5f * gg, gJdotE);
+    io.grad_store(A, i, geps_old + deps, gsig_old + dsig);
 }
 
+// Two backward steps per pass over shared-memory tiles, the mirror of mm_tile2_kernel: phase A' takes
+// nu^{n+1} from memory to nu^n of the extended cells of plane p (into the tile), phase B' takes nu^n
+// from the tile to nu^{n-1} of the tile's own cells of plane p - 1 (into memory). A backward step
+// pulls lambda_d(x) = nu_d(x + v_d), so phase B' reads the v_z = +1 directions from plane q + 1, the
+// newest: the v_z classes swap roles against the forward pass. A cell's loss and gradient terms
+// count once, in its own tile and chunk; its two gradient terms are added in registers in the order
+// of two single steps (the sum after step n, then step n - 1), so the sums are the same bits.
+__device__ __forceinline__ int mm_adj_class(int d) {
+    const int c = mm_zclass(d);
+    return c == 0 ? 0 : (c == 1 ? 2 : 1);  // v_z = +1: read by the very next phase B'
+}
+
+struct MMAdjTileA : MMAdjGlobal {
+    float4* dst[3];  // tile slots of plane p, by adjoint class
+    int local;
+    bool count, carry;  // carry: keep the gradient sums in registers for phase B'
+    mutable float ge_out = 0.f, gs_out = 0.f;
+    __device__ bool counts() const { return count; }
+    __device__ void put_nu(const AdjointArgs&, int d, int, float4 o) const {
+        dst[mm_adj_class(d)][mm_zrank(d) * kTileThreads + local] = o;
+    }
+    __device__ void grad_store(const AdjointArgs& A, int i, float ge, float gs) const {
+        if (carry) {
+            ge_out = ge;
+            gs_out = gs;
+        } else {
+            MMAdjGlobal::grad_store(A, i, ge, gs);
+        }
+    }
+};
+
+struct MMAdjTileB : MMAdjGlobal {
+    const float4* src[3];  // tile slots by adjoint class: plane q (0), q - 1 (1), q + 1 (2)
+    int local;
+    bool carry;
+    float ge_in, gs_in;
+    __device__ void lam(const AdjointArgs&, const Neighbourhood&, float4 (&lam)[12]) const {
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            constexpr int off = mm_zrank(d) * kTileThreads + (kMMV[d][0] + kMMV[d][1] * kTileEX);
+            lam[d] = src[mm_adj_class(d)][off + local];
+        });
+    }
+    __device__ void grad_load(const AdjointArgs& A, int i, float& ge, float& gs) const {
+        if (carry) {
+            ge = ge_in;
+            gs = gs_in;
+        } else {
+            MMAdjGlobal::grad_load(A, i, ge, gs);
+        }
+    }
+};
+
+template <int M>
+__global__ void __launch_bounds__(kTileThreads, 2) mm_adjoint2_kernel(AdjointArgs A1, AdjointArgs A2, TileArgs T) {
+    extern __shared__ __align__(16) unsigned char mm_adj_smem[];
+    const MMTile<kF32> tile{reinterpret_cast<float4*>(mm_adj_smem)};
+    const int nz = A1.a.g.nz, nxy = A1.a.g.nx * A1.a.g.ny;
+    const TileCell c = tile_cell(A1.a.g, T);
+    const int* off = T.entry_off + (size_t)c.tile * nz;
+    float carry_ge = 0.f, carry_gs = 0.f;  // the sums of this thread's cell of plane p - 1 after phase A'
+    for (int p = c.z0 - 1; p <= c.z1; ++p) {
+        const int pz = tile_wrap(p, nz);
+        const bool own = p >= c.z0 && p < c.z1;
+        float next_ge = 0.f, next_gs = 0.f;
+        {  // phase A': the first backward step (A1) of the extended cells of plane pz
+            const MMAdjTileA io{{}, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)}, (int)threadIdx.x,
+                                c.core && own, true};
+            mm_adjoint_cell<M, false, false>(A1, pz * nxy + c.cxy, 0, io);
+            next_ge = io.ge_out;
+            next_gs = io.gs_out;
+            const int lo = off[pz], hi = off[pz + 1];
+            if (hi > lo) {  // source cells: their own pass, gradient sums in memory
+                __syncthreads();
+                for (int k = lo + threadIdx.x; k < hi; k += kTileThreads) {
+                    const int2 e = T.entries[k];
+                    const MMAdjTileA sio{{}, {io.dst[0], io.dst[1], io.dst[2]}, e.y,
+                                         own && tile_core(e.y, c.bx, c.by, A1.a.g.nx, A1.a.g.ny), false};
+                    mm_adjoint_cell<M, true, false>(A1, A1.a.sv.cell[e.x], e.x, sio);
+                }
+            }
+        }
+        __syncthreads();
+        if (p > c.z0) {  // phase B': the second backward step (A2) of the tile's own cells of plane q
+            const int q = p - 1;
+            const MMAdjTileB io{{}, {tile.slot(0, q), tile.slot(1, q - 1), tile.slot(2, q + 1)}, (int)threadIdx.x,
+                                true, carry_ge, carry_gs};
+            if (c.core) mm_adjoint_cell<M, false, false>(A2, q * nxy + c.cxy, 0, io);
+            const int lo = off[q], hi = off[q + 1];
+            if (hi > lo) {
+                __syncthreads();
+                for (int k = lo + threadIdx.x; k < hi; k += kTileThreads) {
+                    const int2 e = T.entries[k];
+                    if (!tile_core(e.y, c.bx, c.by, A1.a.g.nx, A1.a.g.ny)) continue;
+                    const MMAdjTileB sio{{}, {io.src[0], io.src[1], io.src[2]}, e.y, false, 0.f, 0.f};
+                    mm_adjoint_cell<M, true, false>(A2, A2.a.sv.cell[e.x], e.x, sio);
+                }
+            }
+        }
+        __syncthreads();
+        carry_ge = next_ge;
+        carry_gs = next_gs;
+    }
+}
+
+// Source cells (skipped by the ordinary update through the mask) are stepped back at the end of
+// their block (block_source_cells).
 template <int M>
 __global__ void __launch_bounds__(kBlock, 3) mm_adjoint_kernel(AdjointArgs A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.a.g.n) return;
-    mm_adjoint_cell<M, false, false>(A, i, 0);
-}
-
-template <int M>
-__global__ void __launch_bounds__(kBlock) mm_adjoint_special_kernel(AdjointArgs A) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= A.a.sv.n_special) return;
-    mm_adjoint_cell<M, true, false>(A, A.a.sv.cell[m], m);
+    if (i < A.a.g.n) mm_adjoint_cell<M, false, false>(A, i, 0);
+    block_source_cells(A.a.sv, blockIdx.x, [&](int c, int m) { mm_adjoint_cell<M, true, false>(A, c, m); });
 }
 
 template <int M>
@@ -773,15 +889,9 @@ int mm_launch_step(const StepArgs& a, cudaStream_t st) {
         with_media(a.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             const int nb = blocks_for(a.cell_end - a.cell_begin);
-            if (rho) mm_step_kernel<S, M, false, true><<<nb, kBlock, 0, st>>>(a);
-            else mm_step_kernel<S, M, false, false><<<nb, kBlock, 0, st>>>(a);
+            if (rho) mm_step_kernel<S, M, true><<<nb, kBlock, 0, st>>>(a);
+            else mm_step_kernel<S, M, false><<<nb, kBlock, 0, st>>>(a);
             launched = 1;
-            if (a.sv.n_special > 0) {
-                const int ns = blocks_for(a.sv.n_special);
-                if (rho) mm_step_kernel<S, M, true, true><<<ns, kBlock, 0, st>>>(a);
-                else mm_step_kernel<S, M, true, false><<<ns, kBlock, 0, st>>>(a);
-                launched = 2;
-            }
         });
     });
     return launched;
@@ -893,12 +1003,23 @@ int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st) {
         constexpr int M = decltype(mc)::value;
         mm_adjoint_kernel<M><<<blocks_for(A.a.g.n), kBlock, 0, st>>>(A);
         launched = 1;
-        if (A.a.sv.n_special > 0) {
-            mm_adjoint_special_kernel<M><<<blocks_for(A.a.sv.n_special), kBlock, 0, st>>>(A);
-            launched = 2;
-        }
     });
     return launched;
+}
+
+int mm_launch_adjoint2(const AdjointArgs& A1, const AdjointArgs& A2, const TileArgs& T, cudaStream_t st) {
+    const dim3 grid(T.tiles_x * T.tiles_y, (A1.a.g.nz + T.chunk - 1) / T.chunk);
+    with_media(A1.a.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        static bool done = false;  // the attribute is a property of the kernel: set it once per process
+        if (!done) {
+            cudaFuncSetAttribute(mm_adjoint2_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)MMTile<kF32>::kBytes);
+            done = true;
+        }
+        mm_adjoint2_kernel<M><<<grid, kTileThreads, MMTile<kF32>::kBytes, st>>>(A1, A2, T);
+    });
+    return 1;
 }
 
 int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t st) {
@@ -977,14 +1098,9 @@ int mm_launch_record_step(const StepArgs& a, cudaStream_t st) {
     const bool rho = a.rho_in != nullptr;
     with_media(a.media_mode, [&](auto mc) {
         constexpr int M = decltype(mc)::value;
-        if (rho) mm_record_kernel<M, false, true><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
-        else mm_record_kernel<M, false, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+        if (rho) mm_record_kernel<M, true><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
+        else mm_record_kernel<M, false><<<blocks_for(a.g.n), kBlock, 0, st>>>(a);
         launched = 1;
-        if (a.sv.n_special > 0) {
-            if (rho) mm_record_kernel<M, true, true><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
-            else mm_record_kernel<M, true, false><<<blocks_for(a.sv.n_special), kBlock, 0, st>>>(a);
-            launched = 2;
-        }
     });
     return launched;
 }

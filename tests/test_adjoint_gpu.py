@@ -228,3 +228,33 @@ def test_sqrt_interval_stays_within_the_classic_sqrt_layout(model):
         assert results[k][0] == results[k0][0]
         assert np.array_equal(results[k][1], results[k0][1]) and np.array_equal(results[k][2], results[k0][2])
     L.close()
+
+
+@pytest.mark.parametrize("interval", [-1, 5])
+def test_tiled_backward_equals_single_steps_bitwise(interval):
+    """With fusion mode 3 (planes of at least 16 x 16), pairs of MM backward steps run as tiled
+    passes. The loss and both gradients must equal those of the single-step backward
+    (lbm_set_step_fusion(0)) bit for bit: odd step counts (a single step is left over), a
+    current and an imposed source in the tiles, per-cell eps_r and sigma, every record resident or
+    segments of 5 steps. The oracle adjoint checks the result as in the other tests."""
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    w, f0, plane = small_case("mm", seed=90, shape=(20, 18, 9), plane=(0, 13))
+    steps = 13
+    out = {}
+    for mode in (0, 3):
+        L = lattice_from_workload(w, init=False)
+        L.set_step_fusion(mode)
+        assert L.pass_kind == (None if mode == 0 else "tiled")
+        L.set_populations(np.asarray(f0, np.float32), 3)
+        loss, ge, gs = L.adjoint(steps, plane[0], plane[1], interval)
+        out[mode] = (loss, ge.cpu().numpy(), gs.cpu().numpy())
+        L.close()
+    assert out[3][0] == out[0][0]
+    assert np.array_equal(out[3][1], out[0][1])
+    assert np.array_equal(out[3][2], out[0][2])
+    O = oracle_from_workload(w, init=False, threads=8)
+    O.set_populations(f0, 3)
+    loss_ref, ge_ref, gs_ref = O.loss_and_gradient(steps, *plane)
+    assert abs(out[3][0] - loss_ref) <= LOSS_TOL * loss_ref
+    assert rel_l2(out[3][1], ge_ref) <= GRAD_TOL
+    assert rel_l2(out[3][2], gs_ref) <= GRAD_TOL
