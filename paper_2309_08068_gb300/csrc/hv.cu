@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 3 : 4) hv_tile2_kern
 
 // The block's source cells are recomputed at the end (block_source_cells).
 template <int S, int M>
-__global__ void __launch_bounds__(kBlock) hv_step_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) hv_step_kernel(StepArgs a) {
     const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.cell_end) hv_update<S, M, false>(a, i, 0);
     block_source_cells(a.sv, blockIdx.x, [&](int c, int m) { hv_update<S, M, true>(a, c, m); });
