@@ -273,9 +273,11 @@ int lbm_tiled_layout_check(int nx, int ny);
  * lbm_step does, and
  *   L = sum_{t=1..steps} sum over the cells of plane (plane_axis, plane_index) of |E(t)|^2,
  * with E(t) the field lbm_fields reports after t steps. The gradients dL/d eps_r and dL/d sigma of
- * every cell (n floats each; NULL skips one) are taken at fixed starting populations. The adjoint
+ * every cell (n floats each; NULL skips one, and a NULL grad_sigma also skips summing it) are taken
+ * at fixed starting populations. The adjoint
  * steps back through the transposed collide-and-stream map. What it needs of forward step t is a
- * per-cell record: E and X = D' - mu0 J_ext / 4 for MM (24 bytes per cell), E for HV (12 bytes).
+ * per-cell record: X = D' - mu0 J_ext / 4 for MM (E follows from X and the medium), E for HV (12
+ * bytes per cell each).
  * The steps are cut into segments of K = checkpoint_interval steps, counted from the end (the first
  * segment may be shorter). The forward pass writes the records of the final segment and keeps the
  * population state at the start of every earlier one; going backward, each earlier segment is
@@ -299,9 +301,10 @@ int lbm_adjoint_release(lbm_ctx* ctx);
 int64_t lbm_adjoint_workspace_bytes(const lbm_ctx* ctx);
 /* Segment length of the checkpointed mode for `steps` steps: the longest K whose work space stays
  * within that of segments of ceil(sqrt(steps)) steps (about sqrt(steps) states and as many
- * records, the classic sqrt(T) layout), so the memory grows like sqrt(steps). A record (24 B per cell MM, 12 B HV) is 8 (MM) or 12 (HV) times
- * smaller than a state, so this K is several times sqrt(steps), and the forward pass records that
- * many final steps instead of recomputing them. LBM_EINVAL (negative) for bad arguments. */
+ * records, the classic sqrt(T) layout), so the memory grows like sqrt(steps). A record (12 B per
+ * cell) is 16 (MM) or 12 (HV) times smaller than a state, so this K is several times sqrt(steps),
+ * and the forward pass records that many final steps instead of recomputing them. LBM_EINVAL
+ * (negative) for bad arguments. */
 int lbm_adjoint_sqrt_interval(const lbm_ctx* ctx, int steps);
 
 /* ---------------------------------------------------------------------------------------------

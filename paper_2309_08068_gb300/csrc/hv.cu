@@ -617,7 +617,7 @@ __device__ __forceinline__ void hv_adjoint_cell(const AdjointArgs& A, int i, int
     // Every load is issued up front: the source-cell mask of the main launch only gates the stores,
     // so it adds no round trip before the others.
     const bool skip = !kSpecial && !kTerminal && A.special_mask[i] != 0;
-    const float geps_old = __ldg(&A.grad_eps[i]), gsig_old = __ldg(&A.grad_sigma[i]);
+    const float geps_old = __ldg(&A.grad_eps[i]), gsig_old = A.grad_sigma ? __ldg(&A.grad_sigma[i]) : 0.f;
     // E of f^n: from the forward step's record, or (terminal) from the final state
     float3 E;
     if constexpr (kTerminal) {
@@ -699,9 +699,11 @@ __device__ __forceinline__ void hv_adjoint_cell(const AdjointArgs& A, int i, int
         eout[(size_t)k * n + i] = o;
         hout[(size_t)k * n + i] = p;
     });
-    const float gEdotE = gE.x * F.E.x + gE.y * F.E.y + gE.z * F.E.z;
+    // explicit fused multiply-adds wherever a product meets a sum (the same bits in every kernel)
+    const float gEdotE = __fmaf_rn(gE.z, F.E.z, __fmaf_rn(gE.y, F.E.y, __fmul_rn(gE.x, F.E.x)));
     A.grad_eps[i] = geps_old + (geps_imposed - div_rn(gEdotE, er, 1.f / er));
-    A.grad_sigma[i] = gsig_old + (gJ.x * F.E.x + gJ.y * F.E.y + gJ.z * F.E.z);
+    if (A.grad_sigma)
+        A.grad_sigma[i] = gsig_old + __fmaf_rn(gJ.z, F.E.z, __fmaf_rn(gJ.y, F.E.y, __fmul_rn(gJ.x, F.E.x)));
 }
 
 // Source cells (skipped by the ordinary update through the mask) are stepped back at the end of

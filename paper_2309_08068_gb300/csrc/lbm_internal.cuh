@@ -112,8 +112,9 @@ struct StepArgs {
     int cell_begin, cell_end;  // cells the step and reduction launches cover (a z-slab skips its ghost planes)
 };
 
-// Per-cell record an adjoint step needs from its forward step: MM E and X = D' - mu0 J_ext / 4, HV E.
-constexpr int kRecordFloatsMM = 6;
+// Per-cell record an adjoint step needs from its forward step: MM X = D' - mu0 J_ext / 4 (E is an
+// exact function of X and the medium, recomputed by the same operations), HV E.
+constexpr int kRecordFloatsMM = 3;
 constexpr int kRecordFloatsHV = 3;
 
 // Field output: for each selected field a 3 x n block; null pointers are skipped.
@@ -477,7 +478,7 @@ struct AdjointArgs {
     void* nu_out;          // nu^n
     void* nu_out2;
     float* grad_eps;       // dL/d eps_r per cell, accumulated
-    float* grad_sigma;     // dL/d sigma per cell, accumulated
+    float* grad_sigma;     // dL/d sigma per cell, accumulated (null: not computed)
     const uint8_t* special_mask;  // non-zero at source cells, which the second launch handles
     int plane_axis, plane_index;  // loss plane: cells whose coordinate on plane_axis is plane_index
     int loss_active;              // add the plane loss term of time n

@@ -82,6 +82,15 @@ __device__ __forceinline__ float moment_component(const float (&x)[12]) {
     return pairwise_sum<0, N>(t);
 }
 
+// eps_r E = Dpp = X g and E = Dpp / eps_r, each rounded once (__fmul_rn: never fused into a later
+// sum), so that the backward step can recompute E from the recorded X and get the same bits.
+__device__ __forceinline__ float3 mm_dpp(float3 X, float g) {
+    return make_float3(__fmul_rn(X.x, g), __fmul_rn(X.y, g), __fmul_rn(X.z, g));
+}
+__device__ __forceinline__ float3 mm_e_of_dpp(float3 Dpp, float er, float inv_er) {
+    return make_float3(div_rn(Dpp.x, er, inv_er), div_rn(Dpp.y, er, inv_er), div_rn(Dpp.z, er, inv_er));
+}
+
 template <bool kRho>
 __device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0, const MatCoef& mat, float3 jext) {
     float de[12], db[12];
@@ -100,12 +109,8 @@ __device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0
     const float g = mat.c0.z;  // 1 / (1 + mu0 sigma / (4 eps_r))
     const float er = mat.c0.x, inv_er = mat.c0.y, sigma = mat.c1.x;
     o.X = make_float3(0.5f * dx - 0.5f * jext.x, 0.5f * dy - 0.5f * jext.y, 0.5f * dz - 0.5f * jext.z);
-    o.Dpp.x = o.X.x * g;
-    o.Dpp.y = o.X.y * g;
-    o.Dpp.z = o.X.z * g;
-    o.E.x = div_rn(o.Dpp.x, er, inv_er);
-    o.E.y = div_rn(o.Dpp.y, er, inv_er);
-    o.E.z = div_rn(o.Dpp.z, er, inv_er);
+    o.Dpp = mm_dpp(o.X, g);
+    o.E = mm_e_of_dpp(o.Dpp, er, inv_er);
     o.B = make_float3(bx, by, bz);
     // Explicit fused multiply-adds wherever a product is inexact, so that the result does not
     // depend on the compiler's contraction choices (the batched and single-lattice kernels inline
@@ -196,14 +201,11 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m, const
         io.template put<S>(a, d, i, o);
     });
     if constexpr (kRho) a.rho_out[i] = 2.f * F.rho - rest0;  // f_0^(0)eq = rho_c; stays in place
-    if constexpr (kRecord) {  // what the adjoint of this step needs: E and X
+    if constexpr (kRecord) {  // what the adjoint of this step needs: X (E follows from it)
         const int n = a.g.n;
-        a.rec[i] = F.E.x;
-        a.rec[n + i] = F.E.y;
-        a.rec[2 * n + i] = F.E.z;
-        a.rec[3 * n + i] = F.X.x;
-        a.rec[4 * n + i] = F.X.y;
-        a.rec[5 * n + i] = F.X.z;
+        a.rec[i] = F.X.x;
+        a.rec[n + i] = F.X.y;
+        a.rec[2 * n + i] = F.X.z;
     }
 }
 
@@ -646,11 +648,11 @@ struct MMAdjGlobal {
     }
     __device__ void grad_load(const AdjointArgs& A, int i, float& ge, float& gs) const {
         ge = __ldg(&A.grad_eps[i]);
-        gs = __ldg(&A.grad_sigma[i]);
+        if (A.grad_sigma) gs = __ldg(&A.grad_sigma[i]);
     }
     __device__ void grad_store(const AdjointArgs& A, int i, float ge, float gs) const {
         A.grad_eps[i] = ge;
-        A.grad_sigma[i] = gs;
+        if (A.grad_sigma) A.grad_sigma[i] = gs;
     }
 };
 
@@ -672,7 +674,7 @@ __device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int
     const bool counts = io.counts();
     float geps_old = 0.f, gsig_old = 0.f;
     if (counts) io.grad_load(A, i, geps_old, gsig_old);
-    // E and X of f^n: from the forward step's record, or (terminal) from the final state
+    // E and X of f^n: X from the forward step's record (E recomputed from it), or (terminal) the final state
     float3 E, X;
     if constexpr (kTerminal) {
         float4 f[12];
@@ -681,8 +683,8 @@ __device__ __forceinline__ void mm_adjoint_cell(const AdjointArgs& A, int i, int
         E = F.E;
         X = F.X;
     } else {
-        E = make_float3(__ldg(&a.rec[i]), __ldg(&a.rec[n + i]), __ldg(&a.rec[2 * n + i]));
-        X = make_float3(__ldg(&a.rec[3 * n + i]), __ldg(&a.rec[4 * n + i]), __ldg(&a.rec[5 * n + i]));
+        X = make_float3(__ldg(&a.rec[i]), __ldg(&a.rec[n + i]), __ldg(&a.rec[2 * n + i]));
+        E = mm_e_of_dpp(mm_dpp(X, mat.c0.z), mat.c0.x, mat.c0.y);  // as the forward step computed it
     }
     struct {
         float3 E, X;

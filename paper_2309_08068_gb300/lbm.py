@@ -323,21 +323,22 @@ class Lattice:
         self._check(self.lib.lbm_reduce(self.h, out))
         return float(out[0]), float(out[1]), float(out[2])
 
-    def adjoint(self, steps: int, plane_axis: int, plane_index: int, checkpoint_interval: int = 0):
+    def adjoint(self, steps: int, plane_axis: int, plane_index: int, checkpoint_interval: int = 0,
+                sigma: bool = True):
         """Advance `steps` steps and return (L, dL/d eps_r, dL/d sigma) for the plane loss
         L = sum_t sum_plane |E(t)|^2 (lbm_adjoint); gradients are torch CUDA tensors (n,).
         checkpoint_interval: the segment length K. < 0 keeps every step's record on the device; > 0
         records the final K steps in the forward pass and recomputes each earlier K-step segment
         once from a checkpoint; 0 picks the first when it fits in half the free memory, else
-        K = sqrt_interval(steps)."""
+        K = sqrt_interval(steps). sigma=False skips dL/d sigma (returned as None)."""
         import torch
         ge = torch.empty(self.n, dtype=torch.float32, device=self.device)
-        gs = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        gs = torch.empty(self.n, dtype=torch.float32, device=self.device) if sigma else None
         loss = ctypes.c_double()
         self._inputs_ready()
         self._check(self.lib.lbm_adjoint(self.h, int(steps), int(plane_axis), int(plane_index), int(checkpoint_interval),
-                                         ctypes.byref(loss), ge.data_ptr(), gs.data_ptr(), 1))
-        self._outputs_ready(ge, gs)
+                                         ctypes.byref(loss), ge.data_ptr(), gs.data_ptr() if sigma else None, 1))
+        self._outputs_ready(*(t for t in (ge, gs) if t is not None))
         return loss.value, ge, gs
 
     # -- two steps per pass ----------------------------------------------------------------------

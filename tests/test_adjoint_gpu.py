@@ -258,3 +258,21 @@ def test_tiled_backward_equals_single_steps_bitwise(interval):
     assert abs(out[3][0] - loss_ref) <= LOSS_TOL * loss_ref
     assert rel_l2(out[3][1], ge_ref) <= GRAD_TOL
     assert rel_l2(out[3][2], gs_ref) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_sigma_gradient_can_be_skipped(model):
+    """Without an output for dL/d sigma the adjoint skips its sums; the loss and dL/d eps_r are the
+    same bits as with it."""
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    w, f0, plane = small_case(model, seed=91, shape=(20, 18, 9), plane=(0, 13))
+    out = []
+    for sigma in (True, False):
+        L = lattice_from_workload(w, init=False)
+        L.set_populations(np.asarray(f0, np.float32), 3)
+        loss, ge, gs = L.adjoint(11, plane[0], plane[1], 4, sigma=sigma)
+        assert (gs is None) == (not sigma)
+        out.append((loss, ge.cpu().numpy()))
+        L.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
