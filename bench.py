@@ -869,9 +869,9 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nz", type=int, default=0, help="z extent of the timed lattices (default n: a cube)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--fusion", type=int, choices=[0, 1, 2], default=1,
-                    help="lbm_set_step_fusion mode of the timed lattices: 0 one launch per step, 1 two steps per "
-                         "pass where the intermediate planes fit in L2 (default), 2 whenever possible")
+    ap.add_argument("--fusion", type=int, choices=[0, 1, 2, 3], default=1,
+                    help="lbm_set_step_fusion mode of the timed lattices: 0 one launch per step, 1 the two-step "
+                         "pass measured fastest per model (default), 2 the ring pass, 3 the tiled pass")
     ap.add_argument("--slab-steps", type=int, default=50,
                     help="steps of the z-slab decomposition measurement on the dipole lattice (0 skips it)")
     ap.add_argument("--adjoint-steps", type=int, default=1000,

@@ -272,10 +272,10 @@ enum { kPassNone = 0, kPassRing = 1, kPassTiled = 2 };
 
 // Which two-step pass lbm_step(n >= 2) runs: mode 2 the ring, mode 3 the tiles, wherever each is
 // possible. Mode 1 takes what measured fastest on GB300 with FP32 storage: for MM the tiled pass
-// (256^3 dipole: 0.710 ms per step against 0.745 for the ring pass and 0.932 for single steps;
-// 128^3: 0.122 against 0.130 for single steps), for HV the ring pass where it applies, else single
-// steps (the tiled HV pass is held by shared-memory instruction throughput: 0.682 ms per step at
-// 256^3 against 0.516 for the ring pass, and slower than single steps at 128^3).
+// (256^3 dipole: 0.607 ms per step against 0.763 for the ring pass and 0.925 for single steps;
+// 128^3: 0.093 against 0.103 for single steps), for HV the ring pass where it applies, else single
+// steps (the tiled HV pass is held by shared-memory instruction throughput: 0.542 ms per step at
+// 256^3 against 0.522 for the ring pass).
 int pass_kind(const lbm_ctx* c) {
     if (c->fusion == 0) return kPassNone;
     if (c->fusion == 3) return tiled_possible(c) ? kPassTiled : kPassNone;

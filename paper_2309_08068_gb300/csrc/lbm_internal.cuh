@@ -291,6 +291,12 @@ __device__ __forceinline__ Neighbourhood neighbourhood(const Geometry& g, int i)
     return h;
 }
 
+// Ask L2 to fetch the line holding p ahead of a load of it; nothing waits for it and no register
+// receives it. Callers pass only addresses they are about to load themselves.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Index of the cell at offset (sx, sy, sz) in {-1, 0, 1}^3.
 template <int SX, int SY, int SZ>
 __device__ __forceinline__ int shifted(const Neighbourhood& h) {

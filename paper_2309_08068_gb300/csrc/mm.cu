@@ -134,6 +134,17 @@ __device__ __forceinline__ void mm_pull(const StepArgs& a, const Neighbourhood& 
     });
 }
 
+// Prefetch into L2 what mm_pull of cell i will load.
+template <int S>
+__device__ __forceinline__ void mm_prefetch(const StepArgs& a, int i) {
+    const auto* __restrict__ fin = static_cast<const typename Pack4<S>::T*>(a.fin);
+    const Neighbourhood h = neighbourhood(a.g, i);
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        prefetch_l2(fin + (size_t)d * a.g.n + shifted<-kMMV[d][0], -kMMV[d][1], -kMMV[d][2]>(h));
+    });
+}
+
 template <int S>
 __device__ __forceinline__ void mm_put(const StepArgs& a, int d, int i, float4 v) {
     auto* __restrict__ fout = static_cast<typename Pack4<S>::T*>(a.fout);
@@ -583,6 +594,9 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 2 : 3) mm_tile2_kern
     const int* off = T.entry_off + (size_t)c.tile * nz;
     for (int p = c.z0 - 1; p <= c.z1; ++p) {
         const int pz = tile_wrap(p, nz);
+        // The next plane's phase-A inputs, fetched into L2 while this plane is stepped: a plane's
+        // loads are otherwise a DRAM round trip that two blocks per SM cannot hide.
+        if (p < c.z1) mm_prefetch<S>(aA, tile_wrap(p + 1, nz) * nxy + c.cxy);
         {  // phase A: step t of the extended tile's cells of plane pz
             const MMToTile<S> io{{}, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)}, (int)threadIdx.x};
             mm_update<S, M, false, false, false>(aA, pz * nxy + c.cxy, 0, io);
