@@ -225,10 +225,12 @@ int lbm_destroy(lbm_ctx* ctx);
  *   p at step t into a ring of intermediate planes meant to stay in L2, and plane p at step t + 1
  *   once planes p - 1, p, p + 1 of step t exist. Needs a plane of at least 256 cells per SM and
  *   nz >= 4 (MM) or 5 (HV).
- *   mode 0: never; 1 (default): with FP32 storage, the pass measured fastest on GB300: for MM the
- *   tiled pass where it applies, for HV the ring pass when its intermediate planes (R + 2 planes:
- *   R = 5 for MM, 6 for HV) fit in three quarters of L2; 2: the ring pass wherever it applies;
- *   3: the tiled pass wherever it applies (any storage).
+ *   mode 0: never; 1 (default): with FP32 storage, the pass measured fastest on GB300: the tiled
+ *   pass where its blocks at 8-plane chunks exceed 1.5 waves of resident blocks (smaller lattices
+ *   step faster singly), except that HV with a uniform medium takes the ring pass first; else the
+ *   ring pass when its intermediate planes (R + 2 planes: R = 5 for MM, 6 for HV) fit in three
+ *   quarters of L2; else single steps. 2: the ring pass wherever it applies; 3: the tiled pass
+ *   wherever it applies (any storage).
  * Never for z_ghost slabs or track_rho contexts. The ring pass's dependency waits are
  * bounded (2 s, lbm_set_wait_limit); if one expires every block of the pass stops, the populations
  * of that pass are undefined, and the next lbm_sync, lbm_reduce, lbm_reduce_noalloc or host-side

@@ -268,18 +268,43 @@ bool tiled_possible(const lbm_ctx* c) {
     return !c->z_ghost && !c->track_rho && c->g.nz >= 3 && c->g.nx >= kTileEX && c->g.ny >= kTileEY;
 }
 
+// Whether a tiled pass has more than 1.5 waves of resident blocks at its shortest chunks (8 planes).
+// Below that its extra phase-A planes and a ragged last wave cost more than the second step saves:
+// on GB300 it measured slower than single steps on 32^3 to 80^3 lattices (MM 32^3: 13.3 us per step
+// against 6.2) and on 256 x 160 x 16 (MM 49.1 us against 42.7), faster from 96^3 (MM, 1.9 waves).
+bool tiled_fills(const lbm_ctx* c) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int occ = std::max(1, c->model == LBM_MM ? mm_tile2_occupancy(c->storage, c->media_mode)
+                                                   : hv_tile2_occupancy(c->storage, c->media_mode));
+    const long long tiles = (long long)((c->g.nx + kTileTX - 1) / kTileTX) * ((c->g.ny + kTileTY - 1) / kTileTY);
+    const long long blocks = tiles * ((c->g.nz + 7) / 8);
+    return 2 * blocks > 3LL * sms * occ;
+}
+
 enum { kPassNone = 0, kPassRing = 1, kPassTiled = 2 };
 
 // Which two-step pass lbm_step(n >= 2) runs: mode 2 the ring, mode 3 the tiles, wherever each is
-// possible. Mode 1 takes what measured fastest on GB300 with FP32 storage: for MM the tiled pass
-// (256^3 dipole: 0.607 ms per step against 0.763 for the ring pass and 0.925 for single steps;
-// 128^3: 0.093 against 0.103 for single steps), for HV the ring pass where it applies, else single
-// steps (the tiled HV pass is held by shared-memory instruction throughput: 0.542 ms per step at
-// 256^3 against 0.522 for the ring pass).
+// possible. Mode 1 takes what measured fastest on GB300 with FP32 storage (ms per step):
+//   MM: the tiled pass where it fills the GPU (256^3 dipole: 0.607 against 0.763 for the ring pass
+//   and 0.925 for single steps; 128^3: 0.093 against 0.103), else the ring pass where it applies.
+//   HV, uniform medium: the ring pass where it applies (256^3 dipole: 0.517 against 0.540 for the
+//   tiled pass, which is held by shared-memory instruction throughput), else the tiled pass where
+//   it fills the GPU (128^3: 0.085 against 0.090 for single steps).
+//   HV, other media: the tiled pass first (272^3 skin-effect lattice with a material table: 0.630
+//   against 0.696 for the ring pass; 208^3: 0.317 against 0.343), then the ring pass.
+// Where none applies, single steps.
 int pass_kind(const lbm_ctx* c) {
     if (c->fusion == 0) return kPassNone;
     if (c->fusion == 3) return tiled_possible(c) ? kPassTiled : kPassNone;
-    if (c->fusion == 1 && c->model == LBM_MM && c->storage == LBM_F32 && tiled_possible(c)) return kPassTiled;
+    if (c->fusion == 2) return ring_eligible(c) ? kPassRing : kPassNone;
+    if (c->storage != LBM_F32) return kPassNone;  // 16-bit storage: single steps (see ring_eligible)
+    const bool ring_first = c->model == LBM_HV && c->media_mode == kUniform;
+    if (ring_first && ring_eligible(c)) return kPassRing;
+    if (tiled_possible(c) && tiled_fills(c)) return kPassTiled;
     return ring_eligible(c) ? kPassRing : kPassNone;
 }
 
@@ -1808,6 +1833,30 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
             return ctx->model == LBM_MM ? mm_launch_record_step(a, ctx->stream) : hv_launch_record_step(a, ctx->stream);
         return ctx->model == LBM_MM ? mm_launch_step(a, ctx->stream) : hv_launch_step(a, ctx->stream);
     };
+    // Pairs of recording steps as one MM tiled pass wherever lbm_step would take that pass (the same
+    // arithmetic: the same states and records, bit for bit).
+    const bool tiled_rec = ctx->model == LBM_MM && pass_kind(ctx) == kPassTiled;
+    const bool tiled_back = ctx->model == LBM_MM && ctx->fusion == 3 && pass_kind(ctx) == kPassTiled;
+    if ((tiled_rec || tiled_back) && (rc = ensure_tiled(ctx)) != LBM_OK) return rc;
+    TileArgs TA{};
+    if (tiled_rec || tiled_back) {
+        TA.tiles_x = tiled_tiles_x(ctx);
+        TA.tiles_y = tiled_tiles_y(ctx);
+        TA.chunk = tiled_chunk(ctx);
+        TA.entry_off = ctx->d_tiled_off;
+        TA.entries = ctx->d_tiled_entries;
+    }
+    // Two recording steps (iterations iter, iter + 1) from in1 to out1 as one tiled pass.
+    auto forward2 = [&](void* in1, void* out1, int64_t iter, void* rec0, void* rec1) {
+        StepArgs aA = base_args(ctx), aB = base_args(ctx);
+        aA.fin = aB.fin = in1;
+        aA.fout = aB.fout = out1;
+        aA.rec = static_cast<float*>(rec0);
+        aB.rec = static_cast<float*>(rec1);
+        fill_scalars(ctx, aA, iter);
+        fill_scalars(ctx, aB, iter + 1);
+        return mm_launch_record_tile2(aA, aB, TA, ctx->stream);
+    };
     int64_t launched = 0;
     const int64_t t0 = ctx->t;
     const int final_first = steps - K;  // first step of the final segment
@@ -1824,10 +1873,17 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
         if ((rc = lbm_step(ctx, len)) != LBM_OK) return rc;
     }
     for (int s = final_first; s < steps; ++s) {
-        launched += forward(ctx->buf[ctx->cur], ctx->buf2[ctx->cur], ctx->buf[1 - ctx->cur], ctx->buf2[1 - ctx->cur],
-                            t0 + s + 1, true, Ly.recs + rec_bytes * (size_t)(s - final_first));
+        char* rec = Ly.recs + rec_bytes * (size_t)(s - final_first);
+        if (tiled_rec && s + 1 < steps) {
+            launched += forward2(ctx->buf[ctx->cur], ctx->buf[1 - ctx->cur], t0 + s + 1, rec, rec + rec_bytes);
+            ctx->t += 2;
+            ++s;
+        } else {
+            launched += forward(ctx->buf[ctx->cur], ctx->buf2[ctx->cur], ctx->buf[1 - ctx->cur], ctx->buf2[1 - ctx->cur],
+                                t0 + s + 1, true, rec);
+            ctx->t += 1;
+        }
         ctx->cur = 1 - ctx->cur;
-        ctx->t += 1;
     }
     if ((rc = check_launch(ctx, (int)launched)) != LBM_OK) return rc;
     launched = 0;
@@ -1856,16 +1912,6 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
     // 0 .. len - 1. With fusion mode 3, pairs of MM backward steps run as tiled passes (same
     // arithmetic and order of the gradient sums: the same bits). It is not the default: on GB300
     // (128^3, per-cell eps_r) a tiled pair takes 296 us against 2 x 141 for single steps.
-    const bool tiled_back = ctx->model == LBM_MM && ctx->fusion == 3 && pass_kind(ctx) == kPassTiled;
-    if (tiled_back && (rc = ensure_tiled(ctx)) != LBM_OK) return rc;
-    TileArgs TA{};
-    if (tiled_back) {
-        TA.tiles_x = tiled_tiles_x(ctx);
-        TA.tiles_y = tiled_tiles_y(ctx);
-        TA.chunk = tiled_chunk(ctx);
-        TA.entry_off = ctx->d_tiled_off;
-        TA.entries = ctx->d_tiled_entries;
-    }
     auto step_args = [&](AdjointArgs& X, int first, int j) {  // the backward step of record slot j
         const int64_t nstep = first + j;  // reverses forward iteration nstep + 1
         X.a = base_args(ctx);
@@ -1895,11 +1941,19 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
         // Recompute the segment from its checkpoint through two scratch states, recording each step.
         void *i1, *i2, *o1, *o2;
         state_ptrs(Ly.ck + state * (size_t)k, &i1, &i2);
+        int w = 0;  // the scratch state written next
         for (int j = 0; j < len; ++j) {
-            state_ptrs(Ly.work + state * (size_t)(j & 1), &o1, &o2);
-            launched += forward(i1, i2, o1, o2, t0 + first + j + 1, false, Ly.recs + rec_bytes * (size_t)j);
+            state_ptrs(Ly.work + state * (size_t)w, &o1, &o2);
+            char* rec = Ly.recs + rec_bytes * (size_t)j;
+            if (tiled_rec && j + 1 < len) {
+                launched += forward2(i1, o1, t0 + first + j + 1, rec, rec + rec_bytes);
+                ++j;
+            } else {
+                launched += forward(i1, i2, o1, o2, t0 + first + j + 1, false, rec);
+            }
             i1 = o1;
             i2 = o2;
+            w ^= 1;
         }
         backward(first, len);
     }

@@ -57,9 +57,10 @@ __device__ __forceinline__ void hv_pull(const StepArgs& a, const Neighbourhood& 
     });
 }
 
-// Prefetch into L2 what hv_pull of cell i will load.
-template <int S>
+// Prefetch into L2 what the update of cell i will load: the populations hv_pull reads and the medium.
+template <int S, int M>
 __device__ __forceinline__ void hv_prefetch(const StepArgs& a, int i) {
+    prefetch_media<M>(a.media, i);
     const auto* __restrict__ ein = static_cast<const typename Pack4<S>::T*>(a.fin);
     const auto* __restrict__ hin = static_cast<const typename Pack2<S>::T*>(a.fin2);
     const Neighbourhood h = neighbourhood(a.g, i);
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 3 : 4) hv_tile2_kern
     const int* off = T.entry_off + (size_t)c.tile * nz;
     for (int p = c.z0 - 1; p <= c.z1; ++p) {
         const int pz = tile_wrap(p, nz);
-        if (p < c.z1) hv_prefetch<S>(aA, tile_wrap(p + 1, nz) * nxy + c.cxy);  // as in mm_tile2_kernel
+        if (p < c.z1) hv_prefetch<S, M>(aA, tile_wrap(p + 1, nz) * nxy + c.cxy);  // as in mm_tile2_kernel
         {  // phase A: step t of the extended tile's cells of plane pz
             const HVToTile<S> io{{}, tile.base4, tile.base2, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)},
                                  (int)threadIdx.x};

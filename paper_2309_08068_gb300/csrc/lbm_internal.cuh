@@ -297,6 +297,18 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Prefetch into L2 the medium of cell i (nothing for a uniform medium).
+template <int M>
+__device__ __forceinline__ void prefetch_media(const MediaView& m, int i) {
+    if constexpr (M == kTable) {
+        prefetch_l2(&m.id[i]);
+    } else if constexpr (M == kPerCell) {
+        prefetch_l2(&m.eps_r[i]);
+        prefetch_l2(&m.mu_r[i]);
+        prefetch_l2(&m.sigma[i]);
+    }
+}
+
 // Index of the cell at offset (sx, sy, sz) in {-1, 0, 1}^3.
 template <int SX, int SY, int SZ>
 __device__ __forceinline__ int shifted(const Neighbourhood& h) {
@@ -716,6 +728,7 @@ constexpr int kFusedThreads = kBlock + 32;
 // stored values in registers.
 struct FusedStash {
     static constexpr bool kStash = true;
+    __device__ bool keeps_record() const { return true; }  // a recording step writes this cell's record
     unsigned slot;  // shared address of this thread's slot 0; slot k lies k * kBlock * 8 bytes on
     __device__ void stash_put(int k, float x, float y) const {
         asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(slot + k * kBlock * 8), "f"(x), "f"(y));
@@ -727,6 +740,7 @@ struct FusedStash {
 // The same hooks for the single-step paths, which keep every value in registers.
 struct NoStash {
     static constexpr bool kStash = false;
+    __device__ bool keeps_record() const { return true; }  // a recording step writes this cell's record
     __device__ void stash_put(int, float, float) const {}
     __device__ void stash_get(int, float&, float&) const {}
 };
@@ -957,6 +971,9 @@ int mm_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, c
 int hv_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st);
 int mm_tile2_occupancy(int storage, int media_mode);
 int hv_tile2_occupancy(int storage, int media_mode);
+// The MM tiled pass that also writes both steps' adjoint records (aA.rec, aB.rec; FP32 storage only,
+// else 0 launches).
+int mm_launch_record_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st);
 int hv_launch_record_step(const StepArgs& a, cudaStream_t st);
 int mm_launch_adjoint(const AdjointArgs& A, cudaStream_t st);
 // Two MM backward steps in one pass over shared-memory tiles: A1 the step of nu^{n+1} -> nu^n (its

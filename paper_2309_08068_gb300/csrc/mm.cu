@@ -134,9 +134,10 @@ __device__ __forceinline__ void mm_pull(const StepArgs& a, const Neighbourhood& 
     });
 }
 
-// Prefetch into L2 what mm_pull of cell i will load.
-template <int S>
+// Prefetch into L2 what the update of cell i will load: the populations mm_pull reads and the medium.
+template <int S, int M>
 __device__ __forceinline__ void mm_prefetch(const StepArgs& a, int i) {
+    prefetch_media<M>(a.media, i);
     const auto* __restrict__ fin = static_cast<const typename Pack4<S>::T*>(a.fin);
     const Neighbourhood h = neighbourhood(a.g, i);
     static_for<0, 12>([&](auto dc) {
@@ -213,6 +214,7 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m, const
     });
     if constexpr (kRho) a.rho_out[i] = 2.f * F.rho - rest0;  // f_0^(0)eq = rho_c; stays in place
     if constexpr (kRecord) {  // what the adjoint of this step needs: X (E follows from it)
+        if (!io.keeps_record()) return;
         const int n = a.g.n;
         a.rec[i] = F.X.x;
         a.rec[n + i] = F.X.y;
@@ -550,6 +552,8 @@ struct MMToTile : NoStash {
     using T = typename Pack4<S>::T;
     T* dst[3];  // slots of plane p, by class
     int local;  // extended-tile position of the cell
+    bool own;   // a cell of the block's own tile and planes: a recording pass writes its record
+    __device__ bool keeps_record() const { return own; }
     template <int S2>
     __device__ void pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) const {
         mm_pull<S>(a, h, f);
@@ -583,7 +587,9 @@ struct MMFromTile : NoStash {
     }
 };
 
-template <int S, int M>
+// kRecord: both steps also write the adjoint's per-cell records (aA.rec, aB.rec), each cell's once,
+// by the block that owns it.
+template <int S, int M, bool kRecord = false>
 __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 2 : 3) mm_tile2_kernel(StepArgs aA, StepArgs aB,
                                                                                     TileArgs T) {
     using TT = typename Pack4<S>::T;
@@ -596,17 +602,20 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 2 : 3) mm_tile2_kern
         const int pz = tile_wrap(p, nz);
         // The next plane's phase-A inputs, fetched into L2 while this plane is stepped: a plane's
         // loads are otherwise a DRAM round trip that two blocks per SM cannot hide.
-        if (p < c.z1) mm_prefetch<S>(aA, tile_wrap(p + 1, nz) * nxy + c.cxy);
+        if (p < c.z1) mm_prefetch<S, M>(aA, tile_wrap(p + 1, nz) * nxy + c.cxy);
         {  // phase A: step t of the extended tile's cells of plane pz
-            const MMToTile<S> io{{}, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)}, (int)threadIdx.x};
-            mm_update<S, M, false, false, false>(aA, pz * nxy + c.cxy, 0, io);
+            const bool own_plane = p >= c.z0 && p < c.z1;
+            const MMToTile<S> io{{}, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)}, (int)threadIdx.x,
+                                 own_plane && c.core};
+            mm_update<S, M, false, false, kRecord>(aA, pz * nxy + c.cxy, 0, io);
             const int lo = off[pz], hi = off[pz + 1];
             if (hi > lo) {  // the source cells among them replace their ordinary update
                 __syncthreads();
                 for (int k = lo + threadIdx.x; k < hi; k += kTileThreads) {
                     const int2 e = T.entries[k];
-                    const MMToTile<S> sio{{}, {io.dst[0], io.dst[1], io.dst[2]}, e.y};
-                    mm_update<S, M, true, false, false>(aA, aA.sv.cell[e.x], e.x, sio);
+                    const MMToTile<S> sio{{}, {io.dst[0], io.dst[1], io.dst[2]}, e.y,
+                                          own_plane && tile_core(e.y, c.bx, c.by, aA.g.nx, aA.g.ny)};
+                    mm_update<S, M, true, false, kRecord>(aA, aA.sv.cell[e.x], e.x, sio);
                 }
             }
         }
@@ -614,7 +623,7 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 2 : 3) mm_tile2_kern
         if (p > c.z0) {  // phase B: step t + 1 of the tile's own cells of plane q = p - 1
             const int q = p - 1;
             const MMFromTile<S> io{{}, {tile.slot(0, q), tile.slot(1, q - 1), tile.slot(2, q + 1)}, (int)threadIdx.x};
-            if (c.core) mm_update<S, M, false, false, false>(aB, q * nxy + c.cxy, 0, io);
+            if (c.core) mm_update<S, M, false, false, kRecord>(aB, q * nxy + c.cxy, 0, io);
             const int lo = off[q], hi = off[q + 1];
             if (hi > lo) {
                 __syncthreads();
@@ -622,7 +631,7 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 2 : 3) mm_tile2_kern
                     const int2 e = T.entries[k];
                     if (!tile_core(e.y, c.bx, c.by, aA.g.nx, aA.g.ny)) continue;
                     const MMFromTile<S> sio{{}, {io.src[0], io.src[1], io.src[2]}, e.y};
-                    mm_update<S, M, true, false, false>(aB, aB.sv.cell[e.x], e.x, sio);
+                    mm_update<S, M, true, false, kRecord>(aB, aB.sv.cell[e.x], e.x, sio);
                 }
             }
         }
@@ -828,6 +837,27 @@ struct MMAdjTileB : MMAdjGlobal {
     }
 };
 
+// Prefetch into L2 what phase A' of cell i loads (nu^{n+1} pushed from x + v_d, the record, the
+// medium, the source-cell mask, the gradient sums) and the record phase B' of cell i reads a plane later.
+template <int M>
+__device__ __forceinline__ void mm_adjoint_prefetch(const AdjointArgs& A1, const AdjointArgs& A2, int i) {
+    const int n = A1.a.g.n;
+    const Neighbourhood h = neighbourhood(A1.a.g, i);
+    static_for<0, 12>([&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        prefetch_l2(static_cast<const float4*>(A1.nu_in) + (size_t)d * n + shifted<kMMV[d][0], kMMV[d][1], kMMV[d][2]>(h));
+    });
+    static_for<0, kRecordFloatsMM>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        prefetch_l2(&A1.a.rec[(size_t)k * n + i]);
+        prefetch_l2(&A2.a.rec[(size_t)k * n + i]);
+    });
+    prefetch_media<M>(A1.a.media, i);
+    prefetch_l2(&A1.special_mask[i]);
+    prefetch_l2(&A1.grad_eps[i]);
+    if (A1.grad_sigma) prefetch_l2(&A1.grad_sigma[i]);
+}
+
 template <int M>
 __global__ void __launch_bounds__(kTileThreads, 2) mm_adjoint2_kernel(AdjointArgs A1, AdjointArgs A2, TileArgs T) {
     extern __shared__ __align__(16) unsigned char mm_adj_smem[];
@@ -840,6 +870,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) mm_adjoint2_kernel(AdjointArg
         const int pz = tile_wrap(p, nz);
         const bool own = p >= c.z0 && p < c.z1;
         float next_ge = 0.f, next_gs = 0.f;
+        if (p < c.z1) mm_adjoint_prefetch<M>(A1, A2, tile_wrap(p + 1, nz) * nxy + c.cxy);  // as in mm_tile2_kernel
         {  // phase A': the first backward step (A1) of the extended cells of plane pz
             const MMAdjTileA io{{}, {tile.slot(0, p), tile.slot(1, p), tile.slot(2, p)}, (int)threadIdx.x,
                                 c.core && own, true};
@@ -1068,11 +1099,12 @@ int mm_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F,
     return 1;
 }
 
-template <int S, int M>
+template <int S, int M, bool kRecord = false>
 void mm_tile2_prepare() {
     static bool done = false;  // the attribute is a property of the kernel: set it once per process
     if (!done) {
-        cudaFuncSetAttribute(mm_tile2_kernel<S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MMTile<S>::kBytes);
+        cudaFuncSetAttribute(mm_tile2_kernel<S, M, kRecord>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)MMTile<S>::kBytes);
         done = true;
     }
 }
@@ -1098,6 +1130,17 @@ int mm_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, c
             mm_tile2_prepare<S, M>();
             mm_tile2_kernel<S, M><<<grid, kTileThreads, MMTile<S>::kBytes, st>>>(aA, aB, T);
         });
+    });
+    return 1;
+}
+
+int mm_launch_record_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st) {
+    if (aA.storage != kF32 || !aA.rec || !aB.rec) return 0;
+    const dim3 grid(T.tiles_x * T.tiles_y, (aA.g.nz + T.chunk - 1) / T.chunk);
+    with_media(aA.media_mode, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        mm_tile2_prepare<kF32, M, true>();
+        mm_tile2_kernel<kF32, M, true><<<grid, kTileThreads, MMTile<kF32>::kBytes, st>>>(aA, aB, T);
     });
     return 1;
 }

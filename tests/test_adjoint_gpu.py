@@ -231,9 +231,34 @@ def test_sqrt_interval_stays_within_the_classic_sqrt_layout(model):
 
 
 @pytest.mark.parametrize("interval", [-1, 5])
+def test_tiled_recording_equals_single_steps_bitwise(interval):
+    """Where lbm_step takes the MM tiled pass (the default mode on a lattice that fills the GPU),
+    the adjoint records pairs of forward steps as tiled passes, in the final segment and in every
+    recomputed one, and steps back one step per launch. Loss and gradients must equal those of
+    single steps (lbm_set_step_fusion(0)) bit for bit: odd step counts and segment lengths leave
+    single recording steps, and the sources lie in the tiles."""
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    w, f0, plane = small_case("mm", seed=91, shape=(96, 96, 96), plane=(0, 13))
+    steps = 13
+    out = {}
+    for mode in (0, 1):
+        L = lattice_from_workload(w, init=False)
+        L.set_step_fusion(mode)
+        assert L.pass_kind == (None if mode == 0 else "tiled")
+        L.set_populations(np.asarray(f0, np.float32), 3)
+        loss, ge, gs = L.adjoint(steps, plane[0], plane[1], interval)
+        out[mode] = (loss, ge.cpu().numpy(), gs.cpu().numpy(), L.populations_host())
+        L.close()
+    assert out[1][0] == out[0][0]
+    for k in (1, 2, 3):
+        assert np.array_equal(out[1][k], out[0][k]), k
+    assert np.isfinite(out[0][0]) and np.abs(out[0][1]).max() > 0
+
+
+@pytest.mark.parametrize("interval", [-1, 5])
 def test_tiled_backward_equals_single_steps_bitwise(interval):
-    """With fusion mode 3 (planes of at least 16 x 16), pairs of MM backward steps run as tiled
-    passes. The loss and both gradients must equal those of the single-step backward
+    """With fusion mode 3 (planes of at least 16 x 16), pairs of MM forward steps record and pairs of
+    backward steps run as tiled passes. The loss and both gradients must equal those of single steps
     (lbm_set_step_fusion(0)) bit for bit: odd step counts (a single step is left over), a
     current and an imposed source in the tiles, per-cell eps_r and sigma, every record resident or
     segments of 5 steps. The oracle adjoint checks the result as in the other tests."""

@@ -104,34 +104,40 @@ def test_fused_pairs_match_the_oracle(model):
 
 def test_fusion_switches_on_only_where_allowed():
     from paper_2309_08068_gb300.lbm import Lattice
-    def kind(shape, mode=1, **kw):
-        L = Lattice("mm", shape, **kw)
+    def kind(shape, mode=1, model="mm", eps_r=None, **kw):
+        L = Lattice(model, shape, eps_r, **kw)
         L.set_step_fusion(mode)
         k = L.pass_kind
         L.close()
         return k
-    assert kind(PLANE + (11,)) == "tiled"                 # MM, FP32, planes of at least 16 x 16
-    assert kind((64, 64, 11)) == "tiled"
-    assert kind((16, 16, 3)) == "tiled"
-    assert kind((15, 64, 11)) is None                      # a 16-wide extended tile needs nx >= 16
-    assert kind((64, 64, 2)) is None                       # and nz >= 3
-    L = Lattice("hv", PLANE + (11,))                       # HV takes the ring pass by default
-    assert L.pass_kind == "ring"
-    L.set_step_fusion(3)
-    assert L.pass_kind == "tiled"
-    L.close()
-    L = Lattice("hv", (64, 64, 11))                        # and single steps where the ring does not apply
-    assert L.pass_kind is None
-    L.close()
-    assert kind(PLANE + (11,), mode=0) is None
-    assert kind(PLANE + (11,), track_rho=True) is None    # rest populations are not carried
-    assert kind(PLANE + (11,), z_ghost=True) is None      # slabs step one plane range at a time
+    # Mode 1, FP32: the tiled pass where its blocks at 8-plane chunks exceed 1.5 waves
+    assert kind((96, 96, 96)) == "tiled"                  # MM: 49 tiles x 12 chunks
+    assert kind((256, 256, 64)) == "tiled"
+    assert kind((64, 64, 64)) is None                     # 200 blocks: single steps
+    assert kind(PLANE + (11,)) == "ring"                  # 456 blocks: the ring pass instead
+    assert kind((128, 128, 128), model="hv") == "tiled"   # HV, uniform medium: no ring on 128^2 planes
+    assert kind((256, 256, 64), model="hv") == "ring"     # HV, uniform medium: the ring pass first
+    eps = np.random.default_rng(3).uniform(1.0, 4.0, 256 * 256 * 64).astype(np.float32)
+    assert kind((256, 256, 64), model="hv", eps_r=eps) == "tiled"  # HV, other media: the tiled pass first
+    assert kind(PLANE + (11,), model="hv") == "ring"
+    assert kind((64, 64, 11), model="hv") is None         # neither applies
+    # Mode 3: the tiled pass wherever a 16 x 16 extended tile and 3 planes fit
+    assert kind((16, 16, 3), mode=3) == "tiled"
+    assert kind((64, 64, 11), mode=3, model="hv") == "tiled"
+    assert kind((15, 64, 11), mode=3) is None
+    assert kind((64, 64, 2), mode=3) is None
+    assert kind((256, 256, 64), mode=0) is None
+    assert kind((256, 256, 64), track_rho=True) is None  # rest populations are not carried
+    assert kind((256, 256, 64), z_ghost=True) is None    # slabs step one plane range at a time
+    assert kind((256, 256, 64), mode=3, z_ghost=True) is None
+    # Mode 2: the ring pass
     assert kind(PLANE + (11,), mode=2) == "ring"          # 7 planes of 7.9 MB fit in L2
     assert kind((64, 64, 11), mode=2) is None             # 4,096 cells per plane cannot fill the GPU
     assert kind(PLANE + (3,), mode=2) is None             # MM runs A 3 planes ahead: nz >= 4
     assert kind(PLANE + (4,), mode=2) == "ring"
     assert kind((512, 512, 6), mode=2) == "ring"          # forced: 7 x 50 MB exceed L2
-    assert kind(PLANE + (11,), storage="f16", storage_scale=2.0 ** 12) is None  # single steps by default
+    # 16-bit storage: single steps by default, either pass when asked for
+    assert kind((256, 256, 64), storage="f16", storage_scale=2.0 ** 12) is None
     assert kind(PLANE + (11,), mode=3, storage="f16", storage_scale=2.0 ** 12) == "tiled"
     assert kind(PLANE + (11,), mode=2, storage="bf16") == "ring"
 
@@ -228,7 +234,7 @@ def test_fused_pairs_equal_single_steps_with_full_source_planes(model, tile):
 
 
 # ---------------------------------------------------------------------------------------------
-# The tiled pass (mode 3; the default for FP32): shared-memory tiles with a one-cell ring
+# The tiled pass (mode 3; mode 1's choice where it fills the GPU): shared-memory tiles with a one-cell ring
 # ---------------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("model", ["mm", "hv"])
