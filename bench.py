@@ -36,8 +36,13 @@ from paper_2309_08068_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "MLUPS"
 BYTES_PER_CELL = {"mm": 384, "hv": 288}  # FP32 populations read + written; vacuum needs no media bytes
-POPULATION_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
+POPULATION_BYTES = {"f32": 4, "bf16": 2, "f16": 2, "f24": 3}
 F16_SCALE = 2.0 ** 20  # keeps populations of 1e-4-amplitude fields in FP16's normal range
+
+
+def storage_scale(storage: str) -> float:
+    """Power-of-two scale of the storages whose range is FP16's (FP16 and the 24-bit split)."""
+    return F16_SCALE if storage in ("f16", "f24") else 0.0
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -226,7 +231,7 @@ def oracle_mlups(n_side: int, budget_s: float, threads: int, steps: int | None =
     return total_updates / total_s / 1e6, done, total_s
 
 
-def storage_accuracy(storages=("f32", "bf16", "f16")):
+def storage_accuracy(storages=("f32", "bf16", "f16", "f24")):
     """Relative L2 error of E and B against the FP64 oracle after the 1500-step dielectric pulse
     (1 x 1 x 1024, eps_r = 2.5 slab) for each storage, both models."""
     from oracle import OracleLattice
@@ -242,7 +247,7 @@ def storage_accuracy(storages=("f32", "bf16", "f16")):
         O.step(w.steps)
         o = O.fields()
         for st in storages:
-            L = lattice_from_workload(w, storage=st, storage_scale=F16_SCALE if st == "f16" else 0.0)
+            L = lattice_from_workload(w, storage=st, storage_scale=storage_scale(st))
             L.step(w.steps)
             g = L.fields_host("EB")
             out[st][model] = {c: float(np.linalg.norm(g[c] - o[c]) / np.linalg.norm(o[c])) for c in "EB"}
@@ -482,7 +487,7 @@ def run_ours(args):
     ncell = n_side * n_side * nz
     stream = torch.cuda.Stream()
     lats = {}
-    scale = F16_SCALE if args.storage == "f16" else 0.0
+    scale = storage_scale(args.storage)
     with torch.cuda.stream(stream):
         for model in ("mm", "hv"):
             w = wl.hertz_dipole(model, n=n_side, period=32.0, nz=nz)
@@ -552,15 +557,15 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     finite = all(L.check_finite() for L in lats.values())
 
-    # 16-bit storage variants on the same workload (shorter timed run each)
+    # 16- and 24-bit storage variants on the same workload (shorter timed run each)
     variants = {}
-    for st in ("bf16", "f16"):
+    for st in ("bf16", "f16", "f24"):
         variants[st] = {}
         for model in ("mm", "hv"):
             with torch.cuda.stream(stream):
                 w = wl.hertz_dipole(model, n=n_side, period=32.0, nz=nz)
                 Lv = lattice_from_workload(w, stream=stream, storage=st,
-                                           storage_scale=F16_SCALE if st == "f16" else 0.0)
+                                           storage_scale=storage_scale(st))
             Lv.set_step_fusion(args.fusion)
             for c in chunks(args.warmup):
                 Lv.step(c)
@@ -574,7 +579,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / kv
             fv = Lv.pass_kind
-            nbytes = BYTES_PER_CELL[model] // 2 // (2 if fv is not None else 1)  # per cell and step
+            nbytes = BYTES_PER_CELL[model] * POPULATION_BYTES[st] // 4 // (2 if fv is not None else 1)  # per cell and step
             variants[st][model] = {"MLUPS": round(ncell / (ms * 1e-3) / 1e6, 2), "ms_per_step": round(ms, 4),
                                    "two_steps_per_pass": fv, "bytes_per_cell_step": nbytes,
                                    "algorithmic_GBps": round(nbytes * ncell / (ms * 1e-3) / 1e9, 1),
@@ -612,10 +617,9 @@ def run_ours(args):
 
     value = job_value(2 * ncell, args.steps, world, elapsed_ms * 1e-3)
     peak, peak_kind = hbm_peak()
-    shrink = 4 // POPULATION_BYTES[args.storage]
     # Algorithmic HBM bytes per cell and step: one read and one write of the populations per step,
     # or per pair of steps when a pass runs two (the intermediate step stays on chip).
-    bpc1 = {m: BYTES_PER_CELL[m] // shrink for m in BYTES_PER_CELL}
+    bpc1 = {m: BYTES_PER_CELL[m] * POPULATION_BYTES[args.storage] // 4 for m in BYTES_PER_CELL}
     bpc = {m: bpc1[m] // (2 if fused[m] else 1) for m in bpc1}
     mm_gbs = bpc["mm"] * ncell / (mm_ms * 1e-3) / 1e9
     hv_gbs = bpc["hv"] * ncell / (hv_ms * 1e-3) / 1e9
@@ -878,7 +882,7 @@ def main():
                     help="steps of the adjoint-cost measurement on the 128^3 random medium (0 skips it)")
     ap.add_argument("--refine-steps", type=int, default=100,
                     help="steps of the batched refinement-sweep measurement (0 skips it)")
-    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16", "f24"], default="f32",
                     help="population storage of the main timed run (arithmetic is FP32 in every case)")
     ap.add_argument("--decomposition", choices=["replicas", "slabs"], default="replicas",
                     help="with N > 1 ranks: independent lattices per rank (replicas, weak scaling) or one "

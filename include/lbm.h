@@ -44,8 +44,15 @@ enum {
 /* Population storage precision; arithmetic is FP32 in every case. LBM_BF16 and LBM_F16 store each
  * population in 16 bits (half the bytes of a bandwidth-bound step) as f * storage_scale, rounded to
  * nearest. Measured on GB300 against the FP64 oracle after the 1500-step dielectric pulse: relative L2
- * error 2-3 % (FP16, scale 2^20) and 10-21 % (BF16); neither keeps FP32's grid-convergence order. */
-enum { LBM_F32 = 0, LBM_BF16 = 1, LBM_F16 = 2 };
+ * error 2-3 % (FP16, scale 2^20) and 10-21 % (BF16); neither keeps FP32's grid-convergence order.
+ * LBM_F24 stores 24 bits per population (three quarters of FP32's bytes): f * storage_scale cut
+ * toward zero to FP16, plus a byte holding the remainder in 256ths of that half's last place,
+ * rounded to nearest (a full 256 moves the half one value on): 19 significant bits, relative error at
+ * most 2^-19. Its range is FP16's, so storage_scale must keep |f| * storage_scale below 65504
+ * (larger values saturate) and well above 2^-24 for the precision to hold. No two-step pass and no z_ghost
+ * slab takes it (lbm_step runs single steps; lbm_create refuses a z_ghost slab with
+ * LBM_EUNSUPPORTED); batches, fields, reductions and population access do. */
+enum { LBM_F32 = 0, LBM_BF16 = 1, LBM_F16 = 2, LBM_F24 = 3 };
 
 /* Per-cell linear media (Section I-B remark: eps = eps_r eps0, mu = mu_r mu0). Each pointer is an
  * array of n floats, or NULL for the uniform default eps_r = 1, mu_r = 1, sigma = 0. on_device
@@ -60,11 +67,12 @@ typedef struct {
 } lbm_media;
 
 /* Context options; pass NULL for all defaults.
- * storage: LBM_F32, LBM_BF16 or LBM_F16.  cuda_stream: a cudaStream_t, or NULL for the legacy
- *   default stream.
- * storage_scale: 16-bit storage keeps f * storage_scale; a power of two (so scaling is exact), 0 for
- *   1. FP16 needs it to keep small populations out of subnormals (FP16's smallest normal is 6.1e-5)
- *   and large ones below 65504; BF16 has FP32's range. Ignored for LBM_F32.
+ * storage: LBM_F32, LBM_BF16, LBM_F16 or LBM_F24.  cuda_stream: a cudaStream_t, or NULL for the
+ *   legacy default stream.
+ * storage_scale: 16- and 24-bit storage keep f * storage_scale; a power of two (so scaling is
+ *   exact), 0 for 1. FP16 and F24 need it to keep small populations out of subnormals (FP16's
+ *   smallest normal is 6.1e-5) and large ones below 65504; BF16 has FP32's range. Ignored for
+ *   LBM_F32.
  * track_rho: MM only; also store the rest populations f_0^(0), f_0^(1), so that rho_c (eq.
  *   MacroscopicFieldsMiller) is kept and lbm_get_populations returns them. Otherwise the rest
  *   populations are not stored (neither enters E, B, D, H or J) and read back as 0.

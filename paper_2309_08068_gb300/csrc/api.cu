@@ -135,11 +135,14 @@ int ensure_device(lbm_ctx* ctx) {
 
 // Bytes per cell of the main population array (MM: 12 groups of 4; HV: 6 groups of 4) and of HV's
 // second array (6 groups of 2).
+// LBM_F24 keeps 3 bytes per value: a plane of halves and a plane of correction bytes per group.
 size_t group_bytes(int model, int storage) {
-    const size_t v4 = storage == LBM_F32 ? sizeof(float4) : 4 * sizeof(uint16_t);
+    const size_t v4 = storage == LBM_F32 ? sizeof(float4) : (storage == LBM_F24 ? 4 * 3 : 4 * sizeof(uint16_t));
     return model == LBM_MM ? 12 * v4 : 6 * v4;
 }
-size_t pair_bytes(int storage) { return 6 * (storage == LBM_F32 ? sizeof(float2) : 2 * sizeof(uint16_t)); }
+size_t pair_bytes(int storage) {
+    return 6 * (storage == LBM_F32 ? sizeof(float2) : (storage == LBM_F24 ? 2 * 3 : 2 * sizeof(uint16_t)));
+}
 
 StepArgs base_args(lbm_ctx* c) {
     StepArgs a;
@@ -244,7 +247,7 @@ size_t fused_plane_bytes(const lbm_ctx* c) {
 // default, the populations are stored in FP32 and the intermediate planes fit in three quarters of
 // L2, where they are meant to stay.
 bool ring_eligible(const lbm_ctx* c) {
-    if (c->fusion == 0 || c->fusion == 3 || c->z_ghost || c->track_rho ||
+    if (c->fusion == 0 || c->fusion == 3 || c->z_ghost || c->track_rho || c->storage == LBM_F24 ||
         c->g.nz < std::max(3, fused_shape(c).L + 1))
         return false;
     int dev = 0, sms = 0, l2 = 0;
@@ -265,7 +268,8 @@ bool ring_eligible(const lbm_ctx* c) {
 
 // The tiled pass needs a whole extended tile of distinct cells in x and y.
 bool tiled_possible(const lbm_ctx* c) {
-    return !c->z_ghost && !c->track_rho && c->g.nz >= 3 && c->g.nx >= kTileEX && c->g.ny >= kTileEY;
+    return !c->z_ghost && !c->track_rho && c->storage != LBM_F24 && c->g.nz >= 3 && c->g.nx >= kTileEX &&
+           c->g.ny >= kTileEY;
 }
 
 // Whether a tiled pass has more than 1.5 waves of resident blocks at its shortest chunks (8 planes).
@@ -756,7 +760,7 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
     const int64_t n = (int64_t)nx * ny * nz;
     if (n > (int64_t)INT32_MAX) return fail(nullptr, LBM_EINVAL, "lbm_create: %lld cells exceed 2^31 - 1", (long long)n);
     const int storage = opts ? opts->storage : LBM_F32;
-    if (storage != LBM_F32 && storage != LBM_BF16 && storage != LBM_F16)
+    if (storage != LBM_F32 && storage != LBM_BF16 && storage != LBM_F16 && storage != LBM_F24)
         return fail(nullptr, LBM_EINVAL, "lbm_create: unknown storage %d", storage);
     double scale = (opts && storage != LBM_F32) ? opts->storage_scale : 0.0;
     if (scale == 0.0) scale = 1.0;
@@ -767,6 +771,8 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
     const int z_ghost = opts ? opts->z_ghost : 0;
     if (z_ghost != 0 && z_ghost != 1) return fail(nullptr, LBM_EINVAL, "lbm_create: z_ghost must be 0 or 1");
     if (z_ghost && nz < 3) return fail(nullptr, LBM_EINVAL, "lbm_create: a z_ghost slab needs nz >= 3");
+    if (z_ghost && storage == LBM_F24)
+        return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: z_ghost slabs do not take LBM_F24 storage");
     double eps0 = opts ? opts->eps0 : 0.0, mu0 = opts ? opts->mu0 : 0.0;
     if (eps0 < 0 || mu0 < 0 || !std::isfinite(eps0) || !std::isfinite(mu0))
         return fail(nullptr, LBM_EINVAL, "lbm_create: eps0, mu0 must be >= 0");

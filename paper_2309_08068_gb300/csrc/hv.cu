@@ -45,16 +45,32 @@ __device__ __forceinline__ int push_index(const Neighbourhood& h) {
     return shifted<a == 0 ? s : 0, a == 1 ? s : 0, a == 2 ? s : 0>(h);
 }
 
+// 24-bit storage: in each of the two arrays the 6 planes of halves, then the 6 planes of correction
+// bytes.
 template <int S>
 __device__ __forceinline__ void hv_pull(const StepArgs& a, const Neighbourhood& h, float4 (&e)[6], float2 (&hy)[6]) {
-    const auto* __restrict__ ein = static_cast<const typename Pack4<S>::T*>(a.fin);
-    const auto* __restrict__ hin = static_cast<const typename Pack2<S>::T*>(a.fin2);
-    static_for<0, 6>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        const int src = pull_index<i>(h);
-        e[i] = Pack4<S>::load(ein + (size_t)i * a.g.n + src, a.inv_scale);
-        hy[i] = Pack2<S>::load(hin + (size_t)i * a.g.n + src, a.inv_scale);
-    });
+    if constexpr (S == kF24) {
+        const size_t n6 = 6 * (size_t)a.g.n;
+        const uint2* __restrict__ ehi = static_cast<const uint2*>(a.fin);
+        const unsigned* __restrict__ elo = reinterpret_cast<const unsigned*>(ehi + n6);
+        const unsigned* __restrict__ hhi = static_cast<const unsigned*>(a.fin2);
+        const unsigned short* __restrict__ hlo = reinterpret_cast<const unsigned short*>(hhi + n6);
+        static_for<0, 6>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            const size_t idx = (size_t)i * a.g.n + pull_index<i>(h);
+            e[i] = F24::load4(ehi, elo, idx, a.inv_scale);
+            hy[i] = F24::load2(hhi, hlo, idx, a.inv_scale);
+        });
+    } else {
+        const auto* __restrict__ ein = static_cast<const typename Pack4<S>::T*>(a.fin);
+        const auto* __restrict__ hin = static_cast<const typename Pack2<S>::T*>(a.fin2);
+        static_for<0, 6>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            const int src = pull_index<i>(h);
+            e[i] = Pack4<S>::load(ein + (size_t)i * a.g.n + src, a.inv_scale);
+            hy[i] = Pack2<S>::load(hin + (size_t)i * a.g.n + src, a.inv_scale);
+        });
+    }
 }
 
 // Prefetch into L2 what the update of cell i will load: the populations hv_pull reads and the medium.
@@ -74,10 +90,18 @@ __device__ __forceinline__ void hv_prefetch(const StepArgs& a, int i) {
 
 template <int S>
 __device__ __forceinline__ void hv_put(const StepArgs& a, int k, int i, float4 e, float2 hy) {
-    auto* __restrict__ eout = static_cast<typename Pack4<S>::T*>(a.fout);
-    auto* __restrict__ hout = static_cast<typename Pack2<S>::T*>(a.fout2);
-    eout[(size_t)k * a.g.n + i] = Pack4<S>::pack(e, a.scale);
-    hout[(size_t)k * a.g.n + i] = Pack2<S>::pack(hy, a.scale);
+    if constexpr (S == kF24) {
+        const size_t n6 = 6 * (size_t)a.g.n, idx = (size_t)k * a.g.n + i;
+        uint2* __restrict__ ehi = static_cast<uint2*>(a.fout);
+        unsigned* __restrict__ hhi = static_cast<unsigned*>(a.fout2);
+        F24::store4(ehi, reinterpret_cast<unsigned*>(ehi + n6), idx, e, a.scale);
+        F24::store2(hhi, reinterpret_cast<unsigned short*>(hhi + n6), idx, hy, a.scale);
+    } else {
+        auto* __restrict__ eout = static_cast<typename Pack4<S>::T*>(a.fout);
+        auto* __restrict__ hout = static_cast<typename Pack2<S>::T*>(a.fout2);
+        eout[(size_t)k * a.g.n + i] = Pack4<S>::pack(e, a.scale);
+        hout[(size_t)k * a.g.n + i] = Pack2<S>::pack(hy, a.scale);
+    }
 }
 
 struct HVFields {
@@ -438,9 +462,10 @@ __global__ void __launch_bounds__(kTileThreads, S == kF32 ? 3 : 4) hv_tile2_kern
     }
 }
 
-// The block's source cells are recomputed at the end (block_source_cells).
+// The block's source cells are recomputed at the end (block_source_cells). 4 resident blocks (64
+// registers); 3 for 24-bit storage, whose decoding would spill at 64.
 template <int S, int M>
-__global__ void __launch_bounds__(kBlock, 4) hv_step_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, S == kF24 ? 3 : 4) hv_step_kernel(StepArgs a) {
     const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.cell_end) hv_update<S, M, false>(a, i, 0);
     block_source_cells(a.sv, blockIdx.x, [&](int c, int m) { hv_update<S, M, true>(a, c, m); });
@@ -852,7 +877,7 @@ int hv_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t s
 
 int hv_fused2_occupancy(int storage, int media_mode) {
     int blocks = 0;
-    with_storage(storage, [&](auto sc) {
+    with_pass_storage(storage, [&](auto sc) {
         with_media(media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, hv_fused2_kernel<S, M>, kFusedThreads, 0);
@@ -862,8 +887,9 @@ int hv_fused2_occupancy(int storage, int media_mode) {
 }
 
 int hv_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, cudaStream_t st) {
+    if (aA.storage == kF24) return 0;  // no 24-bit form of the passes
     const int grid = fused_grid(hv_fused2_occupancy(aA.storage, aA.media_mode));
-    with_storage(aA.storage, [&](auto sc) {
+    with_pass_storage(aA.storage, [&](auto sc) {
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             hv_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
@@ -883,7 +909,7 @@ void hv_tile2_prepare() {
 
 int hv_tile2_occupancy(int storage, int media_mode) {
     int blocks = 0;
-    with_storage(storage, [&](auto sc) {
+    with_pass_storage(storage, [&](auto sc) {
         with_media(media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             hv_tile2_prepare<S, M>();
@@ -895,8 +921,9 @@ int hv_tile2_occupancy(int storage, int media_mode) {
 }
 
 int hv_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st) {
+    if (aA.storage == kF24) return 0;  // no 24-bit form of the passes
     const dim3 grid(T.tiles_x * T.tiles_y, (aA.g.nz + T.chunk - 1) / T.chunk);
-    with_storage(aA.storage, [&](auto sc) {
+    with_pass_storage(aA.storage, [&](auto sc) {
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             hv_tile2_prepare<S, M>();

@@ -26,9 +26,10 @@ constexpr int kBlock = 256;
 
 enum MediaMode { kUniform = 0, kTable = 1, kPerCell = 2 };
 
-// Population storage. Arithmetic is FP32 in every case; 16-bit storage converts at the pull and the
-// store. A stored 16-bit value is f * scale (scale a power of two, so the scaling itself is exact).
-enum StorageKind { kF32 = 0, kBF16 = 1, kF16 = 2 };
+// Population storage. Arithmetic is FP32 in every case; 16- and 24-bit storage convert at the pull
+// and the store. A stored value is f * scale (scale a power of two, so the scaling itself is exact).
+// kF24: an FP16 value h plus an 8-bit correction in units of ulp(h) / 256 (see F24 below).
+enum StorageKind { kF32 = 0, kBF16 = 1, kF16 = 2, kF24 = 3 };
 
 // Lattice shape. Cell coordinates come from the linear index by multiplication with host-computed
 // magic numbers (Granlund and Montgomery, "Division by invariant integers using multiplication"):
@@ -207,12 +208,110 @@ struct Pack2<kBF16> {
     }
 };
 
+// 24-bit storage. A value x (already scaled) is kept as h = x rounded toward zero to FP16 and an
+// unsigned byte q = |x - h| / (ulp(h) / 256) rounded to nearest, where ulp(h) = 2^(max(E, 1) - 25)
+// for h's biased exponent E (2^-24 for zero and subnormal h). x - h is exact in FP32 (h is x cut to
+// fewer digits) and lies in [0, ulp(h)) in magnitude, so q is 0 ... 256; 256 carries into h, which
+// moves one FP16 value away from zero (the bit pattern + 1), with q = 0, exactly. The value
+// h + sign(h) q ulp(h) / 256 then keeps 19 significant bits where FP16 keeps 11 (relative error at
+// most 2^-19 for normal h), and it decodes exactly: it needs at most 20 bits. |x| beyond FP16's
+// largest value saturates there. The halves of a direction group and their bytes live in separate
+// planes (a group's 4 halves as one 8-byte word, its 4 bytes as one 4-byte word), so each is one
+// coalesced access.
+//
+// The common cases are computed without branches and without conversion instructions, on the
+// value's FP32 bits. Write W for the FP32 pattern of |stored value| * 2^-112: for a normal h it is
+// [0][e5 as the exponent field][h's 10 mantissa bits][q][5 zero bits], for a zero or subnormal h the
+// denormal (h's bits * 256 + q) * 2^5; in both cases W = (h without its sign) << 13 | q << 5.
+//   Decode: W from the stored bits, then W * 2^112 * 2^112, the sign, * 2^-112 / scale. The first
+//   product is exact; the second overflows to infinity exactly for h's infinities and NaN (exponent
+//   31, values >= 2^16; a NaN decodes as an infinity), and is exact otherwise. Denormal W needs FP32
+//   denormals kept, which this build does (no flush to zero).
+//   Encode, 2^-14 <= |x| < 2^15 (h normal): |x| * 2^-112 is exact and normal; its bits rounded to
+//   nearest at bit 5 (halves to even) are W. |x| < 2^-14: |x| + 2^-9 rounds |x| to a multiple of
+//   2^-32 (halves to even) and its low 23 bits are h's bits * 256 + q. Either way a carry out of q
+//   runs into h, as the definition's carry does.
+//   |x| >= 2^15, infinities and NaN go to encode_rare, the definition written out.
+static __device__ __noinline__ void f24_encode_rare(float x, unsigned& h, unsigned& q);
+struct F24 {
+    __device__ static float join(unsigned z, float inv) {  // z: h in bits 31..16, q in bits 15..8
+        const float w = __uint_as_float((z >> 3) & 0x0fffffe0u);
+        const float m = (w * 0x1p112f) * 0x1p112f;
+        return (__uint_as_float(__float_as_uint(m) | (z & 0x80000000u)) * 0x1p-112f) * inv;
+    }
+    // Bits of the stored pair of x = v * scale: h in bits 15..0, q in bits 23..16 (for packing).
+    __device__ static unsigned split(float v, float scale) {
+        const float x = v * scale, a = fabsf(x);
+        const unsigned b = __float_as_uint(x);
+        const unsigned zn = __float_as_uint(a * 0x1p-112f);
+        const unsigned wn = zn + 0xfu + ((zn >> 5) & 1u);                         // to nearest at bit 5
+        const unsigned ws = (__float_as_uint(a + 0x1p-9f) & 0x7fffffu) << 5;       // multiple of 2^-32
+        const unsigned w = (a < 0x1p-14f ? ws : wn) | ((b >> 3) & 0x10000000u);    // sign into bit 28
+        unsigned out = (w >> 13) | ((w << 11) & 0x00ff0000u);
+        if (!(a < 0x1p15f)) {
+            unsigned h, q;
+            f24_encode_rare(x, h, q);
+            out = h | (q << 16);
+        }
+        return out;
+    }
+    // Four values: halves at hi[idx], bytes at lo[idx].
+    __device__ static float4 load4(const uint2* hi, const unsigned* lo, size_t idx, float inv) {
+        const uint2 h = __ldg(hi + idx);
+        const unsigned q = __ldg(lo + idx);
+        return make_float4(join(__byte_perm(h.x, q, 0x1040), inv), join(__byte_perm(h.x, q, 0x3250), inv),
+                           join(__byte_perm(h.y, q, 0x1060), inv), join(__byte_perm(h.y, q, 0x3270), inv));
+    }
+    __device__ static void store4(uint2* hi, unsigned* lo, size_t idx, float4 v, float scale) {
+        const unsigned s0 = split(v.x, scale), s1 = split(v.y, scale), s2 = split(v.z, scale), s3 = split(v.w, scale);
+        hi[idx] = make_uint2(__byte_perm(s0, s1, 0x5410), __byte_perm(s2, s3, 0x5410));
+        lo[idx] = __byte_perm(__byte_perm(s0, s1, 0x0062), __byte_perm(s2, s3, 0x0062), 0x5410);
+    }
+    // Two values: halves at hi[idx], bytes at lo[idx].
+    __device__ static float2 load2(const unsigned* hi, const unsigned short* lo, size_t idx, float inv) {
+        const unsigned h = __ldg(hi + idx);
+        const unsigned q = __ldg(lo + idx);
+        return make_float2(join(__byte_perm(h, q, 0x1040), inv), join(__byte_perm(h, q, 0x3250), inv));
+    }
+    __device__ static void store2(unsigned* hi, unsigned short* lo, size_t idx, float2 v, float scale) {
+        const unsigned s0 = split(v.x, scale), s1 = split(v.y, scale);
+        hi[idx] = __byte_perm(s0, s1, 0x5410);
+        lo[idx] = (unsigned short)__byte_perm(s0, s1, 0x0062);
+    }
+};
+
+// The definition itself, for |x| >= 2^15, infinities and NaN (x already scaled).
+static __device__ __noinline__ void f24_encode_rare(float x, unsigned& h, unsigned& q) {
+    const __half hh = __float2half_rz(x);
+    h = __half_as_ushort(hh);
+    const float r = fabsf(x - __half2float(hh));
+    const unsigned e = max((h >> 10) & 0x1fu, 1u);
+    const int k = __float2int_rn(r * __uint_as_float((160u - e) << 23));  // |r| / 2^(e - 33)
+    if (k < 256) {
+        q = (unsigned)max(k, 0);
+    } else if (k == 256 && (h & 0x7fffu) < 0x7bffu) {
+        h += 1;  // the next FP16 value away from zero
+        q = 0;
+    } else {
+        q = 255;  // beyond FP16's largest value
+    }
+}
+
 // Host-side dispatch of a runtime storage kind / media mode to a compile-time constant.
 template <class F>
 inline void with_storage(int s, F&& f) {
     if (s == kBF16) f(std::integral_constant<int, kBF16>{});
     else if (s == kF16) f(std::integral_constant<int, kF16>{});
+    else if (s == kF24) f(std::integral_constant<int, kF24>{});
     else f(std::integral_constant<int, kF32>{});
+}
+// The same for the two-step passes, which keep populations in their storage format in shared
+// memory or L2 and have no 24-bit form (the host never selects a pass for kF24 storage).
+template <class F>
+inline void with_pass_storage(int s, F&& f) {
+    if (s == kBF16) f(std::integral_constant<int, kBF16>{});
+    else if (s == kF16) f(std::integral_constant<int, kF16>{});
+    else if (s == kF32) f(std::integral_constant<int, kF32>{});
 }
 template <class F>
 inline void with_media(int m, F&& f) {

@@ -124,14 +124,26 @@ __device__ __forceinline__ MMFields mm_fields(const float4 (&f)[12], float rest0
 }
 
 // Pull the 12 groups of cell i from the previous step's buffer: direction d from cell i - v_d.
+// 24-bit storage: the 12 planes of halves (8 B per group and cell), then the 12 planes of correction
+// bytes (4 B per group and cell).
 template <int S>
 __device__ __forceinline__ void mm_pull(const StepArgs& a, const Neighbourhood& h, float4 (&f)[12]) {
-    const auto* __restrict__ fin = static_cast<const typename Pack4<S>::T*>(a.fin);
-    static_for<0, 12>([&](auto dc) {
-        constexpr int d = decltype(dc)::value;
-        const int src = shifted<-kMMV[d][0], -kMMV[d][1], -kMMV[d][2]>(h);
-        f[d] = Pack4<S>::load(fin + (size_t)d * a.g.n + src, a.inv_scale);
-    });
+    if constexpr (S == kF24) {
+        const uint2* __restrict__ hi = static_cast<const uint2*>(a.fin);
+        const unsigned* __restrict__ lo = reinterpret_cast<const unsigned*>(hi + 12 * (size_t)a.g.n);
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            const int src = shifted<-kMMV[d][0], -kMMV[d][1], -kMMV[d][2]>(h);
+            f[d] = F24::load4(hi, lo, (size_t)d * a.g.n + src, a.inv_scale);
+        });
+    } else {
+        const auto* __restrict__ fin = static_cast<const typename Pack4<S>::T*>(a.fin);
+        static_for<0, 12>([&](auto dc) {
+            constexpr int d = decltype(dc)::value;
+            const int src = shifted<-kMMV[d][0], -kMMV[d][1], -kMMV[d][2]>(h);
+            f[d] = Pack4<S>::load(fin + (size_t)d * a.g.n + src, a.inv_scale);
+        });
+    }
 }
 
 // Prefetch into L2 what the update of cell i will load: the populations mm_pull reads and the medium.
@@ -148,8 +160,14 @@ __device__ __forceinline__ void mm_prefetch(const StepArgs& a, int i) {
 
 template <int S>
 __device__ __forceinline__ void mm_put(const StepArgs& a, int d, int i, float4 v) {
-    auto* __restrict__ fout = static_cast<typename Pack4<S>::T*>(a.fout);
-    fout[(size_t)d * a.g.n + i] = Pack4<S>::pack(v, a.scale);
+    if constexpr (S == kF24) {
+        uint2* __restrict__ hi = static_cast<uint2*>(a.fout);
+        unsigned* __restrict__ lo = reinterpret_cast<unsigned*>(hi + 12 * (size_t)a.g.n);
+        F24::store4(hi, lo, (size_t)d * a.g.n + i, v, a.scale);
+    } else {
+        auto* __restrict__ fout = static_cast<typename Pack4<S>::T*>(a.fout);
+        fout[(size_t)d * a.g.n + i] = Pack4<S>::pack(v, a.scale);
+    }
 }
 
 // Where a step reads its populations and writes its results: the context's A/B buffers.
@@ -224,10 +242,10 @@ __device__ __forceinline__ void mm_update(const StepArgs& a, int i, int m, const
 
 // 3 resident blocks for FP32 storage; 4 for 16-bit storage, whose halved bytes need more loads in
 // flight per SM to reach the copy bandwidth (256^3 dipole on GB300, BF16: 0.475 against 0.497 ms
-// per step at 3 blocks).
+// per step at 3 blocks); 3 for 24-bit storage, whose decoding would spill at 64 registers.
 // The block's source cells are recomputed at the end (block_source_cells).
 template <int S, int M, bool kRho>
-__global__ void __launch_bounds__(kBlock, S == kF32 ? 3 : 4) mm_step_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, S == kF32 || S == kF24 ? 3 : 4) mm_step_kernel(StepArgs a) {
     const int i = a.cell_begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.cell_end) mm_update<S, M, false, kRho>(a, i, 0);
     block_source_cells(a.sv, blockIdx.x, [&](int c, int m) { mm_update<S, M, true, kRho>(a, c, m); });
@@ -1079,7 +1097,7 @@ int mm_launch_adjoint_terminal(const AdjointArgs& A, int n_plane, cudaStream_t s
 
 int mm_fused2_occupancy(int storage, int media_mode) {
     int blocks = 0;
-    with_storage(storage, [&](auto sc) {
+    with_pass_storage(storage, [&](auto sc) {
         with_media(media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mm_fused2_kernel<S, M>, kFusedThreads, 0);
@@ -1089,8 +1107,9 @@ int mm_fused2_occupancy(int storage, int media_mode) {
 }
 
 int mm_launch_fused2(const StepArgs& aA, const StepArgs& aB, const FusedArgs& F, cudaStream_t st) {
+    if (aA.storage == kF24) return 0;  // no 24-bit form of the passes
     const int grid = fused_grid(mm_fused2_occupancy(aA.storage, aA.media_mode));
-    with_storage(aA.storage, [&](auto sc) {
+    with_pass_storage(aA.storage, [&](auto sc) {
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             mm_fused2_kernel<S, M><<<grid, kFusedThreads, 0, st>>>(aA, aB, F);
@@ -1111,7 +1130,7 @@ void mm_tile2_prepare() {
 
 int mm_tile2_occupancy(int storage, int media_mode) {
     int blocks = 0;
-    with_storage(storage, [&](auto sc) {
+    with_pass_storage(storage, [&](auto sc) {
         with_media(media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             mm_tile2_prepare<S, M>();
@@ -1123,8 +1142,9 @@ int mm_tile2_occupancy(int storage, int media_mode) {
 }
 
 int mm_launch_tile2(const StepArgs& aA, const StepArgs& aB, const TileArgs& T, cudaStream_t st) {
+    if (aA.storage == kF24) return 0;  // no 24-bit form of the passes
     const dim3 grid(T.tiles_x * T.tiles_y, (aA.g.nz + T.chunk - 1) / T.chunk);
-    with_storage(aA.storage, [&](auto sc) {
+    with_pass_storage(aA.storage, [&](auto sc) {
         with_media(aA.media_mode, [&](auto mc) {
             constexpr int S = decltype(sc)::value, M = decltype(mc)::value;
             mm_tile2_prepare<S, M>();

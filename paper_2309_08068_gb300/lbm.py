@@ -43,7 +43,7 @@ class _Options(ctypes.Structure):
                 ("z_ghost", ctypes.c_int)]
 
 
-STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "f24": 3}
 
 
 class _TimeFn(ctypes.Structure):

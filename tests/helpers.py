@@ -59,3 +59,30 @@ def fresnel_interface_errors(run, model, lz):
     a_r = peak_interp(ex[: lz // 2 - int(2 * alpha)])
     a_t = peak_interp(ex[lz // 2 + int(alpha):])
     return abs(a_r - R) / abs(R), abs(a_t - T) / T
+
+
+def f24_value(x, scale):
+    """The value FP32 x keeps under 24-bit population storage with a power-of-two scale, written
+    out from the encoding's definition: h = x * scale rounded toward zero to FP16; k = |x * scale - h|
+    / (ulp(h) / 256) rounded to nearest (halves to even), with ulp(h) = 2^(max(E, 1) - 25) for h's
+    biased exponent E; k = 256 moves h one FP16 value away from zero and k to 0 (beyond FP16's
+    largest value, k saturates at 255); the value is (h + sign(h) k ulp(h) / 256) / scale."""
+    xs = np.atleast_1d(np.asarray(x, np.float32) * np.float32(scale))
+    with np.errstate(over="ignore"):  # beyond FP16's range: inf, cut back to 65504 below
+        h = xs.astype(np.float16)  # nearest; then cut toward zero
+    over = np.abs(h.astype(np.float32)) > np.abs(xs)
+    h[over] = np.nextafter(h[over], np.float16(0))
+    r = np.abs(xs - h.astype(np.float32)).astype(np.float64)  # exact
+    e = np.maximum((h.view(np.uint16).astype(np.int64) >> 10) & 0x1F, 1)
+    step = np.ldexp(1.0, e - 33)
+    k = np.rint(r / step)
+    hmax = np.float16(65504.0)
+    carry = (k == 256) & (np.abs(h) < hmax)
+    away = np.where(np.signbit(h), np.float16(-np.inf), np.float16(np.inf))
+    h[carry] = np.nextafter(h[carry], away[carry])
+    k[carry] = 0
+    k = np.minimum(k, 255)
+    e = np.maximum((h.view(np.uint16).astype(np.int64) >> 10) & 0x1F, 1)
+    step = np.ldexp(1.0, e - 33)
+    out = ((h.astype(np.float64) + np.copysign(k * step, h.astype(np.float64))) / scale).astype(np.float32)
+    return out.reshape(np.shape(x)) if np.ndim(x) else out[0]

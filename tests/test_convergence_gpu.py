@@ -2,7 +2,9 @@
 
 The reflected-amplitude error of the FP64 oracle falls at first order as Lz doubles (pinned on the
 CPU). FP32 storage must reproduce the oracle's error at every resolution, which preserves the
-convergence order. 16-bit storage does not preserve it. Each step rounds every population to 8 (BF16)
+convergence order. 24-bit storage (19 significant bits) keeps the order too: its error must stay
+within 40 % of the oracle's at every size and fall by at least 1.5 per doubling (measured on GB300:
+at most 32 % above, 1.7 to 2.7 per doubling). 16-bit storage does not preserve it. Each step rounds every population to 8 (BF16)
 or 11 (FP16) bits, and that noise grows like the square root of the step count, which itself grows
 with Lz. So storage error overtakes discretisation error after the first refinement (FP16) or
 immediately (BF16). The test prints those errors and checks only what
@@ -19,7 +21,7 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 SIZES = (256, 512, 1024, 2048, 4096)
-SCALE = {"f32": 0.0, "bf16": 0.0, "f16": 2.0 ** 10}  # unit-amplitude pulse: FP16 values O(2^7)
+SCALE = {"f32": 0.0, "bf16": 0.0, "f16": 2.0 ** 10, "f24": 2.0 ** 10}  # unit-amplitude pulse: FP16 values O(2^7)
 
 
 def oracle_run(model):
@@ -47,7 +49,7 @@ def gpu_run(model, storage):
 def test_convergence_order_per_storage(model):
     ref = [fresnel_interface_errors(oracle_run(model), model, lz)[0] for lz in SIZES]
     table = {"f64": ref}
-    for storage in ("f32", "f16", "bf16"):
+    for storage in ("f32", "f24", "f16", "bf16"):
         table[storage] = [fresnel_interface_errors(gpu_run(model, storage), model, lz)[0] for lz in SIZES]
     for k, v in table.items():
         print(f"convergence {model} {k:5s} " + " ".join(f"{e:.3e}" for e in v))
@@ -57,6 +59,11 @@ def test_convergence_order_per_storage(model):
     # grids.
     for e32, e64 in zip(table["f32"], ref):
         assert abs(e32 - e64) <= 0.05 * e64 + 3e-5
+    # 24-bit: the oracle's error within 40 % and first order kept up to Lz = 4096
+    for e24, e64 in zip(table["f24"], ref):
+        assert abs(e24 - e64) <= 0.4 * e64, (e24, e64)
+    for a, b in zip(table["f24"], table["f24"][1:]):
+        assert a / b >= 1.5, table["f24"]
     # 16-bit: never better than the discretisation error; FP16 tracks it on the coarsest grid
     for storage in ("f16", "bf16"):
         assert all(e >= 0.5 * r for e, r in zip(table[storage], ref)), storage
