@@ -343,10 +343,11 @@ class Lattice:
 
     # -- two steps per pass ----------------------------------------------------------------------
     def set_step_fusion(self, mode: int, tile_cells: int = 0) -> None:
-        """0: one launch per step; 1 (default): pairs of steps as one pass, the tiled pass where it
-        applies, else the L2-ring pass where it fits; 2: the ring pass wherever it applies; 3: the
-        tiled pass wherever it applies. tile_cells: cells per work item of the ring pass (multiple of
-        256; 0 keeps the current value) (lbm_set_step_fusion)."""
+        """0: one launch per step; 1 (default, FP32 storage): pairs of steps as one pass, the tiled
+        pass where it fills the GPU (HV with a uniform medium takes the ring pass first), else the
+        L2-ring pass where it fits; 2: the ring pass wherever it applies; 3: the tiled pass wherever
+        it applies. tile_cells: cells per work item of the ring pass (multiple of 256; 0 keeps the
+        current value) (lbm_set_step_fusion)."""
         self._check(self.lib.lbm_set_step_fusion(self.h, int(mode), int(tile_cells)))
 
     def set_wait_limit(self, ns: int) -> None:
