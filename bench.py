@@ -255,6 +255,35 @@ def storage_accuracy(storages=("f32", "bf16", "f16", "f24")):
     return out
 
 
+def slab_storage_accuracy(storages=("f32", "bf16", "f16", "f24")):
+    """Storage precision on the 512 x 64 x 64 slab lattice (64 dielectric slabs, eps_r in [1, 8), plane
+    pulse of amplitude 1e-4): relative L2 error of E and B of one (y, z) column against the FP64 oracle
+    on the exact 1-D reduction (512 x 1 x 1), after 3000 steps for MM and 1000 for HV (HV grows
+    exponentially on this medium, in FP64 too)."""
+    from oracle import OracleLattice
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    out = {st: {} for st in storages}
+    for model, steps in (("mm", 3000), ("hv", 1000)):
+        w3 = wl.slab_pulse(model)
+        w1 = wl.slab_pulse(model, shape=(512, 1, 1))
+        f64 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        O = OracleLattice(model, w1.shape, f64(w1.eps_r), threads=8)
+        O.init_fields(f64(w1.E), f64(w1.B))
+        O.step(steps)
+        o = O.fields()
+        for st in storages:
+            L = lattice_from_workload(w3, storage=st, storage_scale=storage_scale(st))
+            L.step(steps)
+            g = L.fields("EB")
+            out[st][model] = {}
+            for c in "EB":
+                col = g[c].reshape(3, 64, 64, 512)[:, 17, 41, :].cpu().numpy().astype(np.float64)
+                out[st][model][c] = float(np.linalg.norm(col - o[c]) / np.linalg.norm(o[c]))
+            L.close()
+    out["steps"] = {"mm": 3000, "hv": 1000}
+    return out
+
+
 def refinement_sweep(stream, steps: int):
     """The skin-effect mesh-refinement sweep (16 lattices N = 32 ... 272, 95.9 M cells, sigma = 0.1):
     `steps` steps of every lattice, batched (lattices whose planes fill the GPU as two-step passes,
@@ -586,6 +615,7 @@ def run_ours(args):
                                    "steps_timed": kv}
             Lv.close()
     accuracy = storage_accuracy() if rank == 0 else None
+    slab_accuracy = slab_storage_accuracy() if rank == 0 and args.slab_accuracy else None
     refinement = refinement_sweep(stream, args.refine_steps) if args.refine_steps > 0 else None
     adjoint = adjoint_cost(stream, args.adjoint_steps) if args.adjoint_steps > 0 else None
     slabs = slab_decomposition(stream, args.n, args.slab_steps) if args.slab_steps > 0 else None
@@ -692,6 +722,7 @@ def run_ours(args):
             st: {m: dict(v, frac=round(v["algorithmic_GBps"] / peak, 4)) for m, v in variants[st].items()}
             for st in variants},
         "rel_l2_vs_fp64_dielectric_pulse_1500": accuracy,
+        "rel_l2_vs_fp64_slab_pulse_512x64x64": slab_accuracy,
         "refinement_batch": refinement,
         "adjoint": adjoint,
         "slab_decomposition_one_gpu": slabs,
@@ -882,6 +913,8 @@ def main():
                     help="steps of the adjoint-cost measurement on the 128^3 random medium (0 skips it)")
     ap.add_argument("--refine-steps", type=int, default=100,
                     help="steps of the batched refinement-sweep measurement (0 skips it)")
+    ap.add_argument("--slab-accuracy", type=int, default=1,
+                    help="1: storage accuracy on the 512 x 64 x 64 slab pulse against the FP64 oracle (0 skips it)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16", "f24"], default="f32",
                     help="population storage of the main timed run (arithmetic is FP32 in every case)")
     ap.add_argument("--decomposition", choices=["replicas", "slabs"], default="replicas",
