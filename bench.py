@@ -623,7 +623,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: upload fields, K steps, read E and B back
     pinned_E = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
     pinned_B = torch.zeros((3, ncell), dtype=torch.float32).pin_memory()
-    out = {m: np.empty((2, 3, ncell), np.float32) for m in lats}
+    out = {m: torch.empty((2, 3, ncell), dtype=torch.float32).pin_memory() for m in lats}
     e2e_steps = args.steps
     barrier(world)
     torch.cuda.synchronize()
@@ -634,7 +634,7 @@ def run_ours(args):
         lats["mm"].step(c)
         lats["hv"].step(c)
     for m, L in lats.items():
-        L._check(L.lib.lbm_fields(L.h, 3, out[m].ctypes.data, 0))
+        L._check(L.lib.lbm_fields(L.h, 3, out[m].data_ptr(), 0))
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     h2d = 2 * 2 * 3 * ncell * 4
     d2h = 2 * 2 * 3 * ncell * 4
@@ -717,7 +717,7 @@ def run_ours(args):
                                            "sample": f"32^3 dipole lattice per model, {st_steps} steps, {st_s:.1f} s"}},
         "e2e": {"value": round(job_value(2 * ncell, e2e_steps, world, e2e_s), 2), "unit": "Mcell-updates/s",
                 "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
-                "job": f"lbm_init_fields from pinned host E, B + {e2e_steps} steps + lbm_fields E, B to host"},
+                "job": f"lbm_init_fields from pinned host E, B + {e2e_steps} steps + lbm_fields E, B to pinned host memory"},
         "storage_variants": {
             st: {m: dict(v, frac=round(v["algorithmic_GBps"] / peak, 4)) for m, v in variants[st].items()}
             for st in variants},

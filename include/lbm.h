@@ -144,7 +144,9 @@ int lbm_create(int model, int nx, int ny, int nz, const lbm_media* media, const 
 /* Appendix B, first lines: every population := its equilibrium for the given E and B with J = 0
  * (MM: D' = eps_r E, eq. MacroscopicEMiller with J = 0; HV: D = eps0 eps_r E); rest populations 0;
  * t := 0. E and B are 3 x n floats, host (on_device = 0) or device memory. Synchronous for host
- * input; stream-ordered for device input. */
+ * input; stream-ordered for device input. Host input passes through a device staging buffer that
+ * the context keeps for later host-side lbm_init_fields and lbm_fields calls (grown as needed,
+ * freed by lbm_destroy); pinned host memory makes the copy fastest. */
 int lbm_init_fields(lbm_ctx* ctx, const float* E, const float* B, int on_device);
 
 /* Add one source (see lbm_source). Takes effect from the next lbm_step. */
@@ -164,8 +166,8 @@ int lbm_step(lbm_ctx* ctx, int n);
 /* Fields at the current time t: moments of the current populations, with the external current of
  * iteration t + 1 (the one the next collision uses). For each bit of mask in the order E, B, D, H, J,
  * 3 x n floats are written to out. MM: D = eps0 eps_r E, H = B / (mu0 mu_r). HV: D and B are the
- * moments, E = D / eps, H = B / mu. Host output (on_device = 0) waits for the stream; device output
- * is stream-ordered. */
+ * moments, E = D / eps, H = B / mu. Host output (on_device = 0) goes through the context's staging
+ * buffer (see lbm_init_fields) and waits for the stream; device output is stream-ordered. */
 int lbm_fields(lbm_ctx* ctx, unsigned mask, float* out, int on_device);
 
 /* Number of populations per cell in the canonical layout: MM 50, HV 36. */

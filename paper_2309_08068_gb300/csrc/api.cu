@@ -75,6 +75,8 @@ struct lbm_ctx {
     // adjoint work space (records, checkpoints, adjoint states), kept between lbm_adjoint calls
     void* adj_ws = nullptr;
     size_t adj_ws_bytes = 0;
+    float* host_stage = nullptr;  // device staging of host fields for lbm_init_fields / lbm_fields
+    size_t host_stage_bytes = 0;
     // staging of a packed halo face for host-side lbm_halo_pack / lbm_halo_unpack
     void* halo_stage = nullptr;
     size_t halo_stage_bytes = 0;
@@ -720,6 +722,8 @@ void release(lbm_ctx* c) {
     free_dev(c->d_result);
     free_dev(c->adj_ws);
     c->adj_ws_bytes = 0;
+    free_dev(c->host_stage);
+    c->host_stage_bytes = 0;
     free_dev(c->halo_stage);
     c->halo_stage_bytes = 0;
     free_dev(c->fused_planes);
@@ -728,6 +732,25 @@ void release(lbm_ctx* c) {
     free_dev(c->d_tile_special);
     free_dev(c->d_tiled_off);
     free_dev(c->d_tiled_entries);
+}
+
+// The context's device staging buffer for host fields, at least `bytes` long. It is kept between
+// calls (a per-call cudaMalloc / cudaFree pair, with the device-wide wait of cudaFree, cost more
+// than the copy itself) and grown when a call needs more. The caller has waited for the stream's
+// earlier use of it: every host-side call that uses it waits before returning.
+int host_staging(lbm_ctx* c, size_t bytes, float** dev) {
+    if (c->host_stage_bytes < bytes) {
+        free_dev(c->host_stage);
+        c->host_stage_bytes = 0;
+        if (cudaMalloc(&c->host_stage, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->host_stage = nullptr;
+            return fail(c, LBM_ENOMEM, "cannot allocate a staging buffer of %zu bytes", bytes);
+        }
+        c->host_stage_bytes = bytes;
+    }
+    *dev = c->host_stage;
+    return LBM_OK;
 }
 
 // Copy a 3 x n (or k x n) input to a device staging buffer when it is on the host.
@@ -869,12 +892,14 @@ int lbm_init_fields(lbm_ctx* ctx, const float* E, const float* B, int on_device)
     int rc;
     if ((rc = ensure_device(ctx)) != LBM_OK) return rc;
     const size_t cnt = 3 * (size_t)ctx->g.n;
-    float *dE = nullptr, *dB = nullptr;
-    bool oE = false, oB = false;
-    if ((rc = stage_input(ctx, E, on_device, cnt, &dE, &oE)) != LBM_OK) return rc;
-    if ((rc = stage_input(ctx, B, on_device, cnt, &dB, &oB)) != LBM_OK) {
-        if (oE) cudaFree(dE);
-        return rc;
+    const float *dE = E, *dB = B;
+    if (!on_device) {
+        float* st = nullptr;
+        if ((rc = host_staging(ctx, 2 * cnt * sizeof(float), &st)) != LBM_OK) return rc;
+        CUDA_TRY(ctx, cudaMemcpyAsync(st, E, sizeof(float) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(st + cnt, B, sizeof(float) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+        dE = st;
+        dB = st + cnt;
     }
     StepArgs a = base_args(ctx);
     ctx->cur = 0;
@@ -886,11 +911,8 @@ int lbm_init_fields(lbm_ctx* ctx, const float* E, const float* B, int on_device)
             cudaMemsetAsync(ctx->rest1, 0, sizeof(float) * ctx->g.n, ctx->stream) != cudaSuccess)
             rc = fail(ctx, LBM_ECUDA, "lbm_init_fields: %s", cudaGetErrorString(cudaGetLastError()));
     }
-    if (oE || oB) {
-        cudaStreamSynchronize(ctx->stream);
-        if (oE) cudaFree(dE);
-        if (oB) cudaFree(dB);
-    }
+    if (!on_device && cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == LBM_OK)  // the caller may reuse E, B
+        rc = fail(ctx, LBM_ECUDA, "lbm_init_fields: %s", cudaGetErrorString(cudaGetLastError()));
     ctx->t = 0;
     return rc;
 }
@@ -991,12 +1013,7 @@ int lbm_fields(lbm_ctx* ctx, unsigned mask, float* out, int on_device) {
     for (int b = 0; b < 5; ++b) nf += (mask >> b) & 1;
     const size_t cnt = 3 * (size_t)ctx->g.n * nf;
     float* dev = out;
-    if (!on_device) {
-        if (cudaMalloc(&dev, sizeof(float) * cnt) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, LBM_ENOMEM, "lbm_fields: cannot allocate %zu floats", cnt);
-        }
-    }
+    if (!on_device && (rc = host_staging(ctx, sizeof(float) * cnt, &dev)) != LBM_OK) return rc;
     FieldsOut fo{nullptr, nullptr, nullptr, nullptr, nullptr};
     float** slots[5] = {&fo.E, &fo.B, &fo.D, &fo.H, &fo.J};
     size_t off = 0;
@@ -1015,7 +1032,6 @@ int lbm_fields(lbm_ctx* ctx, unsigned mask, float* out, int on_device) {
             rc = fail(ctx, LBM_ECUDA, "lbm_fields: copy: %s", cudaGetErrorString(cudaGetLastError()));
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == LBM_OK)
             rc = fail(ctx, LBM_ECUDA, "lbm_fields: %s", cudaGetErrorString(cudaGetLastError()));
-        cudaFree(dev);
     }
     return rc;
 }
