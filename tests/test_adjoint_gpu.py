@@ -176,15 +176,16 @@ def test_workspace_is_kept_grown_and_released(model):
 
 @pytest.mark.parametrize("model", ["mm", "hv"])
 def test_adjoint_refuses_what_it_does_not_support(model):
-    """16-bit storage, a source cell inside the loss plane, a plane index outside the lattice and a
-    z-slab context are refused with an error, and the context stays usable."""
+    """16- and 24-bit storage, a source cell inside the loss plane, a plane index outside the lattice
+    and a z-slab context are refused with an error, and the context stays usable."""
     from paper_2309_08068_gb300.lbm import Lattice, LbmError
     shape = (6, 5, 4)
     n = 6 * 5 * 4
-    L16 = Lattice(model, shape, storage="bf16")
-    with pytest.raises(LbmError):
-        L16.adjoint(3, 0, 2)
-    L16.close()
+    for storage in ("bf16", "f24"):
+        L16 = Lattice(model, shape, storage=storage)
+        with pytest.raises(LbmError):
+            L16.adjoint(3, 0, 2)
+        L16.close()
     L = Lattice(model, shape)
     src = wl.Source("current", np.array([2 + 6 * (1 + 5 * 1)]), wl.TimeFunction("const", 1.0), w=np.ones((1, 3)))
     L.add_source(src)  # cell (2, 1, 1): in the plane x = 2

@@ -116,3 +116,38 @@ def test_f24_steps_singly_and_batches_bit_for_bit(model):
         for A, B in zip(solo, grouped):
             assert A.time == B.time
             assert np.array_equal(A.populations_host(), B.populations_host()), rep
+
+
+@pytest.mark.parametrize("model", ["mm", "hv"])
+def test_f24_fields_and_reductions_equal_fp32_on_representable_values(model):
+    """A 24-bit lattice and an FP32 lattice holding the same values (values the 24-bit storage keeps
+    exactly) decode to the same populations, so every field, lbm_reduce and lbm_reduce_noalloc must
+    agree bit for bit; sources and per-cell media included."""
+    import ctypes
+    from paper_2309_08068_gb300.lbm import lattice_from_workload
+    w, f = wl.slab_case(model, (20, 12, 9), seed=190, media="random")
+    q = 48 if model == "mm" else 36
+    scale = 2.0 ** 6
+    f = np.asarray(f, np.float32)
+    f[:q] = f24_value(f[:q], scale)
+    lat = {}
+    for storage in ("f32", "f24"):
+        L = lattice_from_workload(w, init=False, storage=storage, storage_scale=scale if storage == "f24" else 0.0)
+        L.set_populations(f, 4)
+        lat[storage] = L
+    assert np.array_equal(lat["f32"].populations_host()[:q], lat["f24"].populations_host()[:q])
+    a, b = lat["f32"].fields_host("EBDHJ"), lat["f24"].fields_host("EBDHJ")
+    for c in "EBDHJ":
+        assert np.array_equal(a[c], b[c]), c
+    assert lat["f32"].reduce() == lat["f24"].reduce()
+    fn = lat["f32"].lib.lbm_reduce_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    outs = []
+    for storage in ("f32", "f24"):
+        host = (ctypes.c_double * 3)()
+        assert fn(lat[storage].h, host, 0) == 0
+        outs.append(tuple(host))
+    assert outs[0] == outs[1]
+    for L in lat.values():
+        L.close()
