@@ -1886,7 +1886,8 @@ extern "C" int lbm_adjoint(lbm_ctx* ctx, int steps, int plane_axis, int plane_in
     auto seg_first = [&](int k) { return std::max(0, final_first - (n_ck - k) * K); };
     // Forward pass: the state at the start of every earlier segment is kept, and the segment is
     // stepped as lbm_step steps it (two-step passes where they apply: the same bits as single
-    // steps); the final segment is stepped one step per launch, writing its records.
+    // steps); the final segment is stepped writing its records, in pairs as recording tiled passes
+    // where lbm_step takes the MM tiled pass, otherwise one step per launch.
     for (int k = 0; k < n_ck; ++k) {
         const int len = (k + 1 < n_ck ? seg_first(k + 1) : final_first) - seg_first(k);
         char* slot = Ly.ck + state * (size_t)k;
