@@ -436,7 +436,11 @@ def adjoint_cost(stream, steps: int):
                 if call == 0:
                     losses.append(loss)  # both modes start from the same state here
             first_ms, adj_ms = calls
-            res[mode] = {"adjoint_ms_per_step": round(adj_ms, 4), "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
+            layout = {"resident": "every step's record on the device, nothing recomputed",
+                      f"checkpoint_{k_sqrt}": f"classic sqrt(T) layout: segments of {k_sqrt} steps, as many states and records",
+                      "checkpoint_sqrt": f"segments of {k_win} steps: the longest within the classic layout's work space"}[mode]
+            res[mode] = {"layout": layout, "adjoint_ms_per_step": round(adj_ms, 4),
+                         "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
                          "first_call_ms_per_step": round(first_ms, 4),
                          "workspace_gb": round(L.adjoint_workspace_bytes / 1e9, 3),
                          "gradient_finite": bool(torch.isfinite(ge).all().item())}
